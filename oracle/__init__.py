@@ -1,0 +1,379 @@
+"""CPU oracle of the LumiPath light-field sampling path (arXiv 1903.03837).
+
+TEST INFRASTRUCTURE. Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. It shares no code
+with the CUDA library (``paper_1903_03837_gb300``) and does not import it; the
+two meet only in the seeded inputs of ``lf_inputs``.
+
+The arithmetic lives in ``lf_oracle.c`` (plain C, FP64 for every quantity
+that decides a neighbour; see that file's header for the paper passage each
+function follows). This wrapper compiles it with gcc on first use and
+marshals numpy arrays through ctypes. Functions:
+
+* ``sf_phase``, ``sf_point``, ``sf_points``  -- SF point set, Section 2 equation
+* ``camera_ray``, ``trace_pixel``            -- pinhole ray and sphere hits, Section 2
+* ``knn``                                    -- brute-force K nearest SF points
+* ``kernel_sigma``, ``tent_weights``         -- distance filter kernel, Section 2
+* ``render_pixels``, ``render_views``        -- 25-tap blend (K=5), Section 2
+* ``render_backward``                        -- adjoint of the blend w.r.t. the table
+* ``f16_*``, ``e4m3_*``, ``quantize_rows``   -- per-row FP16 / E4M3 table storage
+* ``lobe_table``                             -- the synthetic lobe radiance field
+* ``psnr``                                   -- image error against an FP64 render
+
+Parity unpinned: none. Each function is pinned in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liblf_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+          "-fno-math-errno"]
+
+
+def build(force: bool = False) -> str:
+    """Compile lf_oracle.c into _build/liblf_oracle.so (gcc, no contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Lobes(C.Structure):
+    _fields_ = [("L", C.c_uint32), ("C", C.c_uint32), ("seed", C.c_uint64),
+                ("ap", C.c_void_p), ("ad", C.c_void_p), ("kp", C.c_void_p),
+                ("kd", C.c_void_p), ("col", C.c_void_p)]
+
+
+class _Scene(C.Structure):
+    _fields_ = [("R", C.c_double), ("O", C.c_double * 3), ("M", C.c_uint32),
+                ("N", C.c_uint32), ("C", C.c_uint32), ("K", C.c_int),
+                ("Po", C.c_void_p), ("Pd", C.c_void_p), ("dtype", C.c_int),
+                ("table", C.c_void_p), ("scales", C.c_void_p), ("lobes", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            vp, u32, u64, i64, dbl = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64, C.c_double
+            sig = {
+                "lfo_sf_phase": (dbl, [u64]),
+                "lfo_sf_point": (None, [u32, u32, vp]),
+                "lfo_sf_points": (None, [u32, vp]),
+                "lfo_camera_ray": (None, [vp, u32, u32, u32, u32, vp]),
+                "lfo_intersect": (C.c_int, [C.c_float, vp, vp, vp, vp, vp]),
+                "lfo_normalize_hit": (None, [vp, vp, vp]),
+                "lfo_knn": (C.c_int, [vp, u32, vp, C.c_int, vp, vp]),
+                "lfo_kernel_sigma": (dbl, [u32]),
+                "lfo_tent_weights": (None, [vp, C.c_int, u32, vp]),
+                "lfo_f16_decode": (dbl, [C.c_uint16]),
+                "lfo_f16_encode": (C.c_uint16, [C.c_float]),
+                "lfo_e4m3_decode": (dbl, [C.c_uint8]),
+                "lfo_e4m3_encode": (C.c_uint8, [C.c_float]),
+                "lfo_quantize_rows": (None, [vp, u32, u32, u32, C.c_int, vp, vp]),
+                "lfo_splitmix64": (u64, [u64, u64]),
+                "lfo_lobe_texel": (None, [vp, vp, vp, u32, u32, vp]),
+                "lfo_lobe_table_rows": (None, [vp, vp, vp, u32, u32, u32, vp]),
+                "lfo_render_pixels": (i64, [vp, vp, vp, vp, i64, vp, vp]),
+                "lfo_render_backward_pixels": (None, [vp, vp, vp, vp, i64, vp, vp]),
+                "lfo_trace_pixel": (C.c_int, [dbl, vp, vp, u32, u32, u32, u32, vp, vp, vp, vp, vp]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _threads(n: Optional[int]) -> int:
+    return max(1, int(n if n else (os.cpu_count() or 1)))
+
+
+# --------------------------------------------------------------------------
+# SF points, camera, intersection, k-NN, weights
+# --------------------------------------------------------------------------
+def sf_phase(i: int) -> float:
+    return lib().lfo_sf_phase(int(i))
+
+
+def sf_point(n: int, i: int) -> np.ndarray:
+    p = np.zeros(3)
+    lib().lfo_sf_point(n, i, _p(p))
+    return p
+
+
+_points_cache = {}
+
+
+def sf_points(n: int) -> np.ndarray:
+    """[n,3] FP64 SF points (cached; read-only)."""
+    P = _points_cache.get(n)
+    if P is None:
+        P = np.zeros((n, 3))
+        lib().lfo_sf_points(n, _p(P))
+        P.setflags(write=False)
+        _points_cache[n] = P
+    return P
+
+
+def camera_ray(view, x: int, y: int) -> np.ndarray:
+    d = np.zeros(3, np.float32)
+    lib().lfo_camera_ray(_p(view.floats14()), view.width, view.height, x, y, _p(d))
+    return d
+
+
+def intersect(R: float, O, e, d):
+    O32 = np.asarray(O, np.float32)
+    e = np.asarray(e, np.float32)
+    d = np.asarray(d, np.float32)
+    ho = np.zeros(3, np.float32)
+    hd = np.zeros(3, np.float32)
+    hit = lib().lfo_intersect(float(np.float32(R)), _p(O32), _p(e), _p(d), _p(ho), _p(hd))
+    return bool(hit), ho, hd
+
+
+def trace_pixel(R: float, O, view, x: int, y: int):
+    """(hit, dir, h_o, h_d, q_o, q_d) of one pixel (FP32 ray/hits, FP64 unit hits)."""
+    O64 = np.asarray(O, np.float64)
+    d = np.zeros(3, np.float32)
+    ho = np.zeros(3, np.float32)
+    hd = np.zeros(3, np.float32)
+    qo = np.zeros(3)
+    qd = np.zeros(3)
+    hit = lib().lfo_trace_pixel(R, _p(O64), _p(view.floats14()), view.width, view.height,
+                                x, y, _p(d), _p(ho), _p(hd), _p(qo), _p(qd))
+    return bool(hit), d, ho, hd, qo, qd
+
+
+def normalize_hit(h, O) -> np.ndarray:
+    h = np.asarray(h, np.float32)
+    O = np.asarray(O, np.float64)
+    q = np.zeros(3)
+    lib().lfo_normalize_hit(_p(h), _p(O), _p(q))
+    return q
+
+
+def knn(P: np.ndarray, q, K: int = 5):
+    """Brute-force K nearest rows of P to q: (indices, squared distances)."""
+    P = np.ascontiguousarray(P, np.float64)
+    q = np.ascontiguousarray(q, np.float64)
+    idx = np.zeros(16, np.int32)
+    d2 = np.zeros(16)
+    cnt = lib().lfo_knn(_p(P), P.shape[0], _p(q), K, _p(idx), _p(d2))
+    return idx[:cnt].copy(), d2[:cnt].copy()
+
+
+def kernel_sigma(n: int) -> float:
+    return lib().lfo_kernel_sigma(n)
+
+
+def tent_weights(d2, n: int) -> np.ndarray:
+    d2 = np.ascontiguousarray(d2, np.float64)
+    w = np.zeros(len(d2))
+    lib().lfo_tent_weights(_p(d2), len(d2), n, _p(w))
+    return w
+
+
+# --------------------------------------------------------------------------
+# Quantisers
+# --------------------------------------------------------------------------
+def f16_decode(codes) -> np.ndarray:
+    f = lib().lfo_f16_decode
+    return np.array([f(int(c)) for c in np.asarray(codes, np.uint16).ravel()])
+
+
+def f16_encode(x) -> np.ndarray:
+    f = lib().lfo_f16_encode
+    return np.array([f(float(v)) for v in np.asarray(x, np.float32).ravel()], np.uint16)
+
+
+def e4m3_decode(codes) -> np.ndarray:
+    f = lib().lfo_e4m3_decode
+    return np.array([f(int(c)) for c in np.asarray(codes, np.uint8).ravel()])
+
+
+def e4m3_encode(x) -> np.ndarray:
+    f = lib().lfo_e4m3_encode
+    return np.array([f(float(v)) for v in np.asarray(x, np.float32).ravel()], np.uint8)
+
+
+def quantize_rows(T: np.ndarray, dtype: str):
+    """Per-row quantisation of an FP32 [M,N,C] table -> (codes, scales[M])."""
+    T = np.ascontiguousarray(T, np.float32)
+    M, N, Cc = T.shape
+    code_t = {"f16": np.uint16, "e4m3": np.uint8}[dtype]
+    codes = np.zeros(T.shape, code_t)
+    scales = np.zeros(M, np.float32)
+    lib().lfo_quantize_rows(_p(T), M, N, Cc, 1 if dtype == "f16" else 2, _p(codes), _p(scales))
+    return codes, scales
+
+
+def splitmix64(seed: int, ctr: int) -> int:
+    return int(lib().lfo_splitmix64(seed & (2**64 - 1), ctr & (2**64 - 1)))
+
+
+# --------------------------------------------------------------------------
+# Lobe field
+# --------------------------------------------------------------------------
+class _LobesHold:
+    def __init__(self, lobes):
+        self.ap = np.ascontiguousarray(lobes.ap, np.float64)
+        self.ad = np.ascontiguousarray(lobes.ad, np.float64)
+        self.kp = np.ascontiguousarray(lobes.kp, np.float64)
+        self.kd = np.ascontiguousarray(lobes.kd, np.float64)
+        self.col = np.ascontiguousarray(lobes.col, np.float64)
+        self.s = _Lobes(lobes.L, lobes.C, lobes.noise_seed, _p(self.ap).value, _p(self.ad).value,
+                        _p(self.kp).value, _p(self.kd).value, _p(self.col).value)
+
+
+def lobe_texel(lobes, M: int, N: int, i: int, j: int) -> np.ndarray:
+    h = _LobesHold(lobes)
+    out = np.zeros(16)
+    lib().lfo_lobe_texel(C.byref(h.s), _p(sf_points(M)), _p(sf_points(N)), i, j, _p(out))
+    return out[:lobes.C].copy()
+
+
+def lobe_table(lobes, M: int, N: int, rows: Optional[Sequence[int]] = None,
+               threads: Optional[int] = None) -> np.ndarray:
+    """FP32 table [M,N,C] (or [len(rows),N,C]) of the lobe field, FP64 then rounded."""
+    h = _LobesHold(lobes)
+    Po, Pd = sf_points(M), sf_points(N)
+    L = lib()
+    if rows is None:
+        out = np.zeros((M, N, lobes.C), np.float32)
+        nt = _threads(threads)
+        chunks = np.array_split(np.arange(M), nt * 4)
+
+        def work(ch):
+            if len(ch):
+                L.lfo_lobe_table_rows(C.byref(h.s), _p(Po), _p(Pd), N, int(ch[0]), int(ch[-1]) + 1,
+                                      _p(out[ch[0]:]))
+        with ThreadPoolExecutor(nt) as ex:
+            list(ex.map(work, chunks))
+        return out
+    rows = list(rows)
+    out = np.zeros((len(rows), N, lobes.C), np.float32)
+    for k, i in enumerate(rows):
+        L.lfo_lobe_table_rows(C.byref(h.s), _p(Po), _p(Pd), N, int(i), int(i) + 1, _p(out[k:]))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Rendering
+# --------------------------------------------------------------------------
+class Scene:
+    """Sphere S (R, O), SF set sizes M, N and the table the blend reads.
+
+    table kinds: ``f32`` (FP32 [M,N,C]), ``f16`` / ``e4m3`` (codes [M,N,C] and
+    FP32 per-row scales), ``lobe`` (the lobe field evaluated in FP64 on demand).
+    """
+
+    def __init__(self, M: int, N: int, Cc: int, kind: str = "f32", table=None, scales=None,
+                 lobes=None, R: float = 1.0, O=(0.0, 0.0, 0.0), K: int = 5):
+        self.M, self.N, self.C, self.K, self.kind = M, N, Cc, K, kind
+        self.R, self.O = float(R), tuple(float(o) for o in O)
+        self.Po, self.Pd = sf_points(M), sf_points(N)
+        dt = {"f32": 0, "f16": 1, "e4m3": 2, "lobe": 3}[kind]
+        self._hold = []
+        tptr = sptr = lptr = None
+        if kind == "f32":
+            self.table = np.ascontiguousarray(table, np.float32).reshape(M, N, Cc)
+            tptr = _p(self.table).value
+        elif kind in ("f16", "e4m3"):
+            self.table = np.ascontiguousarray(table, np.uint16 if kind == "f16" else np.uint8)
+            self.table = self.table.reshape(M, N, Cc)
+            self.scales = np.ascontiguousarray(scales, np.float32)
+            tptr, sptr = _p(self.table).value, _p(self.scales).value
+        else:
+            self._lh = _LobesHold(lobes)
+            lptr = C.cast(C.pointer(self._lh.s), C.c_void_p).value
+        self.s = _Scene(self.R, (C.c_double * 3)(*self.O), M, N, Cc, K, _p(self.Po).value,
+                        _p(self.Pd).value, dt, tptr, sptr, lptr)
+
+
+def _views_arrays(views):
+    vf = np.ascontiguousarray(np.stack([v.floats14() for v in views]), np.float32)
+    wh = np.ascontiguousarray(np.array([[v.width, v.height] for v in views], np.uint32))
+    return vf, wh
+
+
+def render_pixels(scene: Scene, views, pix: np.ndarray, threads: Optional[int] = None):
+    """Render pixels pix [n,3] = (view, x, y): (out [n,C] FP64, idx [n,2K], hits)."""
+    pix = np.ascontiguousarray(pix, np.uint32)
+    n = pix.shape[0]
+    vf, wh = _views_arrays(views)
+    out = np.zeros((n, scene.C))
+    idx = np.zeros((n, 2 * scene.K), np.int32)
+    L = lib()
+    nt = min(_threads(threads), max(1, n // 64))
+    bounds = np.linspace(0, n, nt * 4 + 1).astype(np.int64)
+
+    def work(k):
+        a, b = int(bounds[k]), int(bounds[k + 1])
+        if b <= a:
+            return 0
+        return L.lfo_render_pixels(C.byref(scene.s), _p(vf), _p(wh), _p(pix[a:]), b - a,
+                                   _p(out[a:]), _p(idx[a:]))
+    with ThreadPoolExecutor(nt) as ex:
+        hits = sum(ex.map(work, range(len(bounds) - 1)))
+    return out, idx, int(hits)
+
+
+def render_views(scene: Scene, views, threads: Optional[int] = None):
+    """Render every pixel of every view into an output buffer of
+    max(out_offset + W*H) pixels: (out [P,C] FP64, idx [P,2K], hits)."""
+    import lf_inputs
+    P = lf_inputs.total_pixels(views)
+    out = np.zeros((P, scene.C))
+    idx = np.full((P, 2 * scene.K), -1, np.int32)
+    pix = lf_inputs.pixel_list(views)
+    o, i, hits = render_pixels(scene, views, pix, threads)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    out[offs] = o
+    idx[offs] = i
+    return out, idx, hits
+
+
+def render_backward(scene: Scene, views, pix: np.ndarray, grad_out: np.ndarray) -> np.ndarray:
+    """G = A^T g for the blend A over pixels pix; grad_out [n,C]; G [M,N,C] FP64."""
+    pix = np.ascontiguousarray(pix, np.uint32)
+    g = np.ascontiguousarray(grad_out, np.float64).reshape(pix.shape[0], scene.C)
+    vf, wh = _views_arrays(views)
+    G = np.zeros((scene.M, scene.N, scene.C))
+    lib().lfo_render_backward_pixels(C.byref(scene.s), _p(vf), _p(wh), _p(pix), pix.shape[0],
+                                     _p(g), _p(G))
+    return G
+
+
+def psnr(ref: np.ndarray, test: np.ndarray, hit: np.ndarray) -> float:
+    """10 log10(peak^2 / MSE) over hit pixels and all channels; peak = max of ref
+    over those entries."""
+    ref = np.asarray(ref, np.float64)[hit]
+    test = np.asarray(test, np.float64)[hit]
+    if ref.size == 0:
+        return float("nan")
+    mse = float(np.mean((ref - test) ** 2))
+    peak = float(ref.max())
+    return float("inf") if mse == 0.0 else 10.0 * np.log10(peak * peak / mse)
