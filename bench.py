@@ -1,0 +1,375 @@
+"""Benchmark of the light-field sampling path on the large workload.
+
+Workload: 262,144 origin x 4,096 direction SF points, RGBA lobe-field table
+stored as E4M3 (4 GiB, headline), FP16 (8 GiB) and FP32 (16 GiB) with per-row
+FP32 scales; a 240-frame orbit at 3R, each frame a 3840x2160 stereo pair
+(16,588,800 rays) rendered in one launch. A step renders one frame.
+
+Prints one JSON line: Grays/s over all pixels (value, device-timed with CUDA
+events), the end-to-end figure through the public API with the image read
+back to pinned host memory every step (e2e), the roofline of the render
+kernel against the measured HBM copy bandwidth, the SM clocks seen during the
+timed region, and the CPU oracle timed on a bounded sample (cpu_baseline).
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+Multi-GPU (torchrun): every rank renders its own frames (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lf_inputs  # noqa: E402
+
+METRIC = "Grays/s light-field lookup (FP16/FP8 vs FP32 table at stated PSNR); % HBM peak"
+UNIT = "Grays/s"
+TEXEL_BYTES = {"f32": 16, "f16": 8, "e4m3": 4}
+SCALE_BYTES = {"f32": 0, "f16": 20, "e4m3": 20}
+OUT_BYTES = 16
+
+
+def workload_name(cfg) -> str:
+    return (f"large: {cfg.M:,} x {cfg.N:,} RGBA lobe-field table (E4M3 4 GiB headline; FP16 8 GiB, "
+            f"FP32 16 GiB variants) with per-row FP32 scales; 240-frame orbit at 3R, elevation 20 deg, "
+            f"one 3840x2160 stereo pair per frame ({cfg.rays:,} rays) in one launch")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        time.sleep(0.2)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(hits: int, rays: int, dtype: str) -> int:
+    return hits * (25 * TEXEL_BYTES[dtype] + SCALE_BYTES[dtype] + OUT_BYTES) + (rays - hits) * OUT_BYTES
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    from paper_1903_03837_gb300 import torch_api as api
+    from paper_1903_03837_gb300 import lumipath as lp
+    from paper_1903_03837_gb300 import autotune
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev_index = torch.cuda.current_device()
+    cfg = lf_inputs.config_large()
+    lob = cfg.lobes()
+    M, N = cfg.M, cfg.N
+    t0 = time.time()
+    T32 = api.fill_lobe_table(lob, M, N)
+    tables = {"f32": api.LightField(T32, "f32", borrow=True)}
+    codes = {}
+    for dt in ("f16", "e4m3"):
+        c, s = api.quantize_table(T32, dt)
+        codes[dt] = (c, s)
+        tables[dt] = api.LightField(c, dt, s, borrow=True)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+
+    frames_total = cfg.extra["frames"]
+    my_frames = [(rank * (args.steps + args.warmup) + k) % frames_total for k in range(args.steps + args.warmup)]
+    frame_views = {f: lf_inputs.orbit_frame(f) for f in set(my_frames)}
+    rays = cfg.rays
+    launch = autotune.best_launch(tables[args.dtype], [frame_views[my_frames[0]]], key=f"large-{args.dtype}",
+                                  quick=args.quick_tune)
+    for t in tables.values():
+        t.set_launch(**launch)
+
+    # hits per frame (untimed): from the index output
+    hits = {}
+    idx_buf = torch.empty((rays, 10), dtype=torch.int32, device="cuda")
+    for f, vs in frame_views.items():
+        _, idx = tables["e4m3"].render(vs, with_idx=True, idx=idx_buf)
+        hits[f] = int((idx[:, 0] >= 0).sum())
+    del idx_buf
+
+    outs = [torch.empty((rays, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+    stream = torch.cuda.current_stream()
+
+    def timed(dtype):
+        lf = tables[dtype]
+        for k in range(args.warmup):
+            lf.render(frame_views[my_frames[k]], out=outs[k % 2])
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for k in range(args.steps):
+            f = my_frames[args.warmup + k]
+            lf.render(frame_views[f], out=outs[k % 2])
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        if world > 1:
+            tt = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(tt)
+            torch.distributed.barrier()
+        nbytes = sum(algorithmic_bytes(hits[my_frames[args.warmup + k]], rays, dtype) for k in range(args.steps))
+        return total_ms, per, nbytes
+
+    with ClockSampler(dev_index) as clk:
+        total_ms, per_ms, nbytes = timed(args.dtype)
+    clocks = clk.summary()
+    variants = {}
+    for dt in ("f16", "f32"):
+        if dt == args.dtype:
+            continue
+        tm, pm, nb = timed(dt)
+        variants[dt] = {"grays_s": world * args.steps * rays / (tm * 1e-3) / 1e9,
+                        "ms_per_step": tm / args.steps,
+                        "hbm_frac_of_measured": nb / (sum(pm) * 1e-3) / 1e9 / measured_peaks()[0]}
+
+    # quality of the quantised tables against the FP32-table image (full frame, GPU)
+    f0 = my_frames[0]
+    ref, idx = tables["f32"].render(frame_views[f0], with_idx=True)
+    hitmask = idx[:, 0] >= 0
+    psnr_vs_f32 = {}
+    for dt in ("f16", "e4m3"):
+        img, _ = tables[dt].render(frame_views[f0])
+        r, g = ref[hitmask].double(), img[hitmask].double()
+        mse = float(((r - g) ** 2).mean())
+        psnr_vs_f32[dt] = 10 * math.log10(float(r.max()) ** 2 / mse) if mse > 0 else float("inf")
+    gpu_images = {dt: tables[dt].render(frame_views[f0])[0] for dt in ("f32", "f16", "e4m3")}
+
+    # end to end through the public API: views in, image read back to pinned host memory
+    host = torch.empty((rays, 4), dtype=torch.float32, pin_memory=True)
+    lf = tables[args.dtype]
+    for k in range(min(2, args.warmup)):
+        lf.render(frame_views[my_frames[k]], out=outs[0])
+        host.copy_(outs[0], non_blocking=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t_e2e = time.perf_counter()
+    for k in range(args.steps):
+        lf.render(frame_views[my_frames[args.warmup + k]], out=outs[0])
+        host.copy_(outs[0], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t_e2e
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt)
+
+    peak, peak_kind = measured_peaks()
+    avg_launch_s = sum(per_ms) / len(per_ms) * 1e-3
+    bytes_per_launch = nbytes / args.steps
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    value = world * args.steps * rays / (total_ms * 1e-3) / 1e9
+    hit_frac = float(np.mean([hits[f] for f in my_frames[args.warmup:]]) / rays)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(cfg), "table_storage": args.dtype,
+                   "rays_per_step": rays, "hit_fraction": hit_frac,
+                   "l2": "inputs larger than L2: 4 GiB table, 265 MB image per step, orbit frame changes every step",
+                   "launch": launch, "parallelism": f"replicas x{world} (views sharded, no collective)",
+                   "setup_s": round(setup_s, 2)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "kernel": f"lfk::render_kernel<{args.dtype}>", "avg_launch_ms": avg_launch_s * 1e3},
+        "clocks": clocks,
+        "e2e": {"value": world * args.steps * rays / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * 72, "d2h_bytes_per_step": rays * 16},
+        "gpu_launches": args.steps,
+        "variants": variants,
+        "psnr_vs_f32_table_db": psnr_vs_f32,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], psnr64 = cpu_baseline(cfg, frame_views[f0], gpu_images, args)
+        line["psnr_vs_fp64_db"] = psnr64
+    for t in tables.values():
+        t.close()
+    return line
+
+
+def cpu_baseline(cfg, views, gpu_images, args):
+    """The CPU oracle (brute-force K-NN, FP64) on a bounded random sample of the
+    frame's pixels; also the FP64 reference of those pixels for PSNR."""
+    import oracle
+    cores = host_cores()
+    sc = oracle.Scene(cfg.M, cfg.N, 4, "lobe", lobes=cfg.lobes())
+    oracle.sf_points(cfg.M)
+    oracle.sf_points(cfg.N)
+    probe = lf_inputs.sample_pixels(views, 2000, seed=11)
+    t = time.perf_counter()
+    oracle.render_pixels(sc, views, probe, threads=cores)
+    rate = len(probe) / (time.perf_counter() - t)
+    n = int(min(max(4000, rate * args.cpu_seconds), cfg.rays))
+    pix = lf_inputs.sample_pixels(views, n, seed=12)
+    t = time.perf_counter()
+    ref, idx, hits = oracle.render_pixels(sc, views, pix, threads=cores)
+    dt = time.perf_counter() - t
+    offs = lf_inputs.pixel_offsets(views, pix)
+    hit = idx[:, 0] >= 0
+    psnr = {}
+    for k, img in gpu_images.items():
+        g = img.cpu().numpy().astype(np.float64)[offs]
+        psnr[k] = oracle.psnr(ref, g, hit)
+    base = {"value": n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n:,} random pixels of orbit frame 0 ({hits:,} hits), brute-force FP64 K-NN "
+                      f"over all {cfg.M:,}+{cfg.N:,} SF points, texels from the FP64 lobe field; "
+                      f"{dt:.1f} s on {cores} threads"}
+    return base, psnr
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle as it stands, on the same workload
+# ---------------------------------------------------------------------------
+def run_reference(args, rank: int, world: int):
+    import oracle
+    cfg = lf_inputs.config_large()
+    cores = host_cores()
+    sc = oracle.Scene(cfg.M, cfg.N, 4, "lobe", lobes=cfg.lobes())
+    oracle.sf_points(cfg.M)
+    oracle.sf_points(cfg.N)
+    per_step = max(500, int(args.ref_pixels))
+    steps = []
+    for k in range(args.warmup + args.steps):
+        views = lf_inputs.orbit_frame(k % cfg.extra["frames"])
+        pix = lf_inputs.sample_pixels(views, per_step, seed=100 + k)
+        t = time.perf_counter()
+        oracle.render_pixels(sc, views, pix, threads=cores)
+        if k >= args.warmup:
+            steps.append(time.perf_counter() - t)
+    tot = sum(steps)
+    value = per_step * len(steps) / tot / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(steps) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(cfg), "table_storage": "FP64 lobe field (oracle)",
+                   "rays_per_step": per_step, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step:,} random pixels per step of the orbit frames"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="e4m3", choices=["e4m3", "f16", "f32"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-pixels", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick-tune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * lumipath.h -- C ABI of the GB300 light-field sampling library.
+ *
+ * The library samples the light field of LumiPath (Fink et al., arXiv
+ * 1903.03837, Section 2). A bounding sphere S (radius R, centre O) carries two
+ * spherical-Fibonacci (SF) point sets: M ray origins P_o and N "directions"
+ * P_d (exit points on S). The radiance table L^(i,j) holds one texel per
+ * origin/exit pair. For each camera ray the library
+ *   1. intersects the ray with S (front hit h_o, back hit h_d; tangential rays
+ *      are discarded),
+ *   2. finds the 5 nearest points of P_o to h_o and of P_d to h_d (the inverse
+ *      SF mapping, extended to five neighbours),
+ *   3. weights each neighbour with the distance filter kernel of radius
+ *      R*5^(1/4)*sqrt(4*pi/(sqrt(5)*n)) (= R*sqrt(4*pi/n)), tent-shaped,
+ *   4. blends the 25 texels L^(i_a, j_b) with the product weights.
+ *
+ * All entry points are plain C: device pointers are CUDA global-memory
+ * addresses on the current device, host pointers are ordinary memory, and
+ * `stream` is a cudaStream_t (NULL = legacy default stream). Every call
+ * returns an lf_status and never aborts; lf_last_error() gives the message of
+ * the calling thread's last failure. Work is enqueued on `stream` and is
+ * asynchronous unless stated otherwise.
+ */
+#ifndef LUMIPATH_H
+#define LUMIPATH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lf_status {
+    LF_OK = 0,
+    LF_ERR_INVALID_ARG = 1,    /* a null pointer, a size out of range, a bad enum */
+    LF_ERR_OUT_OF_MEMORY = 2,  /* a device allocation failed */
+    LF_ERR_CUDA = 3,           /* a CUDA runtime call or launch failed */
+    LF_ERR_UNSUPPORTED = 4,    /* valid but not implemented combination */
+    LF_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+    LF_ERR_DEVICE_CHECK = 6    /* a device-side check set the table's status word */
+} lf_status;
+
+/* Storage type of the radiance table. FP16 and E4M3 tables carry one FP32
+ * scale per origin row: texel value = scale[i] * decode(code). */
+typedef enum lf_dtype {
+    LF_DTYPE_F32 = 0,
+    LF_DTYPE_F16 = 1,          /* IEEE 754 binary16 */
+    LF_DTYPE_E4M3 = 2          /* OCP FP8 E4M3FN (bias 7, max 448, no inf) */
+} lf_dtype;
+
+/* lf_table_desc.flags */
+#define LF_TABLE_BORROW 0x1u   /* keep the caller's device pointers instead of copying */
+
+/* Description of a light-field table (Section 2: sphere S with radius R and
+ * origin O; point counts M and N; the texture L^(i,j) of M x N texels). */
+typedef struct lf_table_desc {
+    double radius;             /* R > 0, finite */
+    double center[3];          /* O, finite */
+    uint32_t n_origins;        /* M, 1 <= M <= 2^24 */
+    uint32_t n_directions;     /* N, 1 <= N <= 2^24 */
+    uint32_t channels;         /* C in {3, 4} */
+    int32_t dtype;             /* lf_dtype */
+    uint32_t flags;            /* LF_TABLE_* */
+    uint32_t k_nearest;        /* neighbours per hit; 0 means 5; only 5 is supported */
+} lf_table_desc;
+
+/* A pinhole camera. Pixel (x, y) of a W x H image looks along
+ *   v = forward + ((2(x+0.5))/W - 1) * tan_half_x * right
+ *               + (1 - (2(y+0.5))/H) * tan_half_y * up,
+ * normalised, from `eye`; every operation is one FP32 IEEE operation in
+ * exactly this order (no fused multiply-add). Row 0 is the top of the image.
+ * The pixel's output goes to out[out_offset + y*W + x]. */
+typedef struct lf_view {
+    float eye[3];
+    float right[3];
+    float up[3];
+    float forward[3];
+    float tan_half_x;
+    float tan_half_y;
+    uint32_t width;            /* 1 <= W <= 65536 */
+    uint32_t height;           /* 1 <= H <= 65536 */
+    uint64_t out_offset;       /* in pixels */
+} lf_view;
+
+/* Launch shape of the render and backward kernels (chosen by the autotuner).
+ * block = tile_w * tile_h threads; one thread per ray; each warp covers a
+ * warp_w x (32/warp_w) pixel sub-tile. */
+typedef struct lf_launch {
+    uint32_t tile_w;           /* pixels per CTA tile in x; multiple of warp_w */
+    uint32_t tile_h;           /* pixels per CTA tile in y; multiple of 32/warp_w */
+    uint32_t warp_w;           /* 1, 2, 4, 8, 16 or 32 */
+    uint32_t order;            /* 0: tiles in raster order per view; 1: Z-order */
+    uint32_t persistent;       /* 0: one CTA per tile; 1: CTAs pull tiles from a queue */
+    uint32_t ctas_per_sm;      /* persistent grid = SMs * ctas_per_sm (0: occupancy) */
+} lf_launch;
+
+typedef struct lf_table lf_table;
+
+/* Create a table on the current device.
+ * radiance_dev: device array [M][N][C_s] in row-major order (origin row i,
+ *   direction column j, channel c), where C_s = C for F32 and for C = 4, and
+ *   C_s = C for the copied F16/E4M3 forms; element type per dtype (float,
+ *   uint16 binary16 bits, uint8 E4M3 bits).
+ * row_scales_dev: device array [M] of FP32 scales; required for F16/E4M3,
+ *   ignored (may be NULL) for F32.
+ * Without LF_TABLE_BORROW the table and scales are copied (FP16/E4M3 texels
+ *   padded to 4 channels) and the caller may free its arrays once the stream
+ *   reaches this call. With LF_TABLE_BORROW the caller's arrays are used in
+ *   place (F32 with C in {3,4}, or F16/E4M3 with C = 4) and must outlive the
+ *   table; the caller may update their contents between renders (table fitting).
+ * Also builds the SF point caches of both sets on `stream`.
+ * Errors: LF_ERR_INVALID_ARG (null desc/out/radiance, bad sizes, R <= 0 or
+ *   non-finite, missing scales, unsupported channel count, k_nearest != 0/5),
+ *   LF_ERR_OUT_OF_MEMORY, LF_ERR_CUDA. On error *out is NULL. */
+lf_status lf_create_table(const lf_table_desc *desc, const void *radiance_dev,
+                          const float *row_scales_dev, void *stream, lf_table **out);
+
+/* Render n_views views (Section 2, image synthesis by sampling L^).
+ * views_host: host array of n_views lf_view (read during the call only).
+ * out_dev: device FP32 [P][C], P = max(out_offset + W*H) over the views; rays
+ *   that miss S get all C channels 0.
+ * idx_dev: optional device int32 [P][10]: the 5 origin indices then the 5
+ *   direction indices of each ray, each set in ascending (squared chord
+ *   distance, index) order; -1 for a miss. NULL to skip.
+ * Views must not overlap in the output. n_views <= 65536.
+ * Errors: LF_ERR_INVALID_ARG, LF_ERR_CUDA. */
+lf_status lf_render(const lf_table *t, const lf_view *views_host, uint32_t n_views,
+                    float *out_dev, int32_t *idx_dev, void *stream);
+
+/* Gradient of the render with respect to the table: for every hit ray and
+ * every tap (a, b), grad_table[i_a][j_b][c] += W_ab * grad_out[ray][c]
+ * (the adjoint of the linear blend). grad_out_dev: device FP32 [P][C];
+ * grad_table_dev: device FP32 [M][N][C], accumulated (not cleared) with
+ * warp-aggregated atomic adds, so the summation order is not fixed.
+ * Errors: LF_ERR_INVALID_ARG, LF_ERR_CUDA. */
+lf_status lf_render_backward(const lf_table *t, const lf_view *views_host, uint32_t n_views,
+                             const float *grad_out_dev, float *grad_table_dev, void *stream);
+
+/* Destroy a table (NULL-safe). Synchronises the device before freeing. */
+void lf_destroy(lf_table *t);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *lf_last_error(void);
+
+/* Launch shape used by lf_render / lf_render_backward on this table.
+ * Errors: LF_ERR_INVALID_ARG for an inconsistent shape. */
+lf_status lf_set_launch(lf_table *t, const lf_launch *cfg);
+lf_status lf_get_launch(const lf_table *t, lf_launch *cfg);
+
+/* Synchronise `stream` and report the table's device status word: LF_OK, or
+ * LF_ERR_DEVICE_CHECK if a kernel recorded a failed check since the last
+ * call (the word is then cleared). */
+lf_status lf_sync_status(lf_table *t, void *stream);
+
+/* Per-row quantisation of an FP32 table for storage (not part of the paper;
+ * the storage forms of the precision study). src_dev [M][N][C] FP32;
+ * codes_dev [M][N][4] (uint16 binary16 bits or uint8 E4M3 bits; channel 3 is 0
+ * when C = 3); scales_dev [M]. scale = amax (F16) or amax/448 (E4M3) over the
+ * row's N*C values, 1 if amax = 0; code = RNE(x / scale), E4M3 saturating.
+ * Errors: LF_ERR_INVALID_ARG, LF_ERR_CUDA. */
+lf_status lf_quantize_table(const float *src_dev, uint32_t M, uint32_t N, uint32_t C,
+                            int32_t dtype, void *codes_dev, float *scales_dev, void *stream);
+
+/* Synthetic radiance field (a stand-in for the path-traced light field of
+ * Section 2, which needs scenes that are not available):
+ *   T(i,j,c) = sum_l col[l][c] * exp(kp[l] (p^o_i . ap[l] - 1))
+ *                              * exp(kd[l] (dhat_ij . ad[l] - 1)) + 0.01 u(i,j,c)
+ * with dhat_ij the unit ray direction from p^o_i to p^d_j (the ray r_k of
+ * Section 2) and u the SplitMix64 uniform of counter (i<<32 | j<<4 | c) in the
+ * stream seeded by `noise_seed`. Evaluated in FP64, stored as FP32
+ * out_dev [M][N][C]. Host arrays: ap, ad [L][3]; kp, kd [L]; col [L][C]; L <= 64.
+ * Errors: LF_ERR_INVALID_ARG, LF_ERR_OUT_OF_MEMORY, LF_ERR_CUDA. */
+lf_status lf_fill_lobe_table(uint32_t M, uint32_t N, uint32_t C, uint32_t L,
+                             const double *ap, const double *ad, const double *kp,
+                             const double *kd, const double *col, uint64_t noise_seed,
+                             float *out_dev, void *stream);
+
+/* Number of SMs of the current device (0 without one) and the library
+ * version string. */
+int lf_device_sm_count(void);
+const char *lf_version(void);
+
+/* sizeof of the ABI structures as compiled into the library, for bindings to
+ * check their layouts: which = 0 lf_table_desc, 1 lf_view, 2 lf_launch;
+ * 0 for any other value. */
+size_t lf_struct_size(int which);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LUMIPATH_H */

@@ -64,7 +64,8 @@ class _Scene(C.Structure):
     _fields_ = [("R", C.c_double), ("O", C.c_double * 3), ("M", C.c_uint32),
                 ("N", C.c_uint32), ("C", C.c_uint32), ("K", C.c_int),
                 ("Po", C.c_void_p), ("Pd", C.c_void_p), ("dtype", C.c_int),
-                ("table", C.c_void_p), ("scales", C.c_void_p), ("lobes", C.c_void_p)]
+                ("table", C.c_void_p), ("scales", C.c_void_p), ("lobes", C.c_void_p),
+                ("rowmap", C.c_void_p)]
 
 
 def lib():
@@ -273,10 +274,13 @@ def lobe_table(lobes, M: int, N: int, rows: Optional[Sequence[int]] = None,
         with ThreadPoolExecutor(nt) as ex:
             list(ex.map(work, chunks))
         return out
-    rows = list(rows)
+    rows = [int(r) for r in rows]
     out = np.zeros((len(rows), N, lobes.C), np.float32)
-    for k, i in enumerate(rows):
-        L.lfo_lobe_table_rows(C.byref(h.s), _p(Po), _p(Pd), N, int(i), int(i) + 1, _p(out[k:]))
+
+    def one(k):
+        L.lfo_lobe_table_rows(C.byref(h.s), _p(Po), _p(Pd), N, rows[k], rows[k] + 1, _p(out[k:]))
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, range(len(rows))))
     return out
 
 
@@ -288,29 +292,37 @@ class Scene:
 
     table kinds: ``f32`` (FP32 [M,N,C]), ``f16`` / ``e4m3`` (codes [M,N,C] and
     FP32 per-row scales), ``lobe`` (the lobe field evaluated in FP64 on demand).
+    With ``rows`` (a list of origin rows), ``table``/``scales`` hold only those
+    rows, in that order; reading any other row yields NaN.
     """
 
     def __init__(self, M: int, N: int, Cc: int, kind: str = "f32", table=None, scales=None,
-                 lobes=None, R: float = 1.0, O=(0.0, 0.0, 0.0), K: int = 5):
+                 lobes=None, R: float = 1.0, O=(0.0, 0.0, 0.0), K: int = 5, rows=None):
         self.M, self.N, self.C, self.K, self.kind = M, N, Cc, K, kind
         self.R, self.O = float(R), tuple(float(o) for o in O)
         self.Po, self.Pd = sf_points(M), sf_points(N)
         dt = {"f32": 0, "f16": 1, "e4m3": 2, "lobe": 3}[kind]
-        self._hold = []
-        tptr = sptr = lptr = None
+        tptr = sptr = lptr = rptr = None
+        nrows = M
+        if rows is not None:
+            rows = np.asarray(rows, np.int64)
+            nrows = len(rows)
+            self.rowmap = np.full(M, -1, np.int32)
+            self.rowmap[rows] = np.arange(nrows, dtype=np.int32)
+            rptr = _p(self.rowmap).value
         if kind == "f32":
-            self.table = np.ascontiguousarray(table, np.float32).reshape(M, N, Cc)
+            self.table = np.ascontiguousarray(table, np.float32).reshape(nrows, N, Cc)
             tptr = _p(self.table).value
         elif kind in ("f16", "e4m3"):
             self.table = np.ascontiguousarray(table, np.uint16 if kind == "f16" else np.uint8)
-            self.table = self.table.reshape(M, N, Cc)
+            self.table = self.table.reshape(nrows, N, Cc)
             self.scales = np.ascontiguousarray(scales, np.float32)
             tptr, sptr = _p(self.table).value, _p(self.scales).value
         else:
             self._lh = _LobesHold(lobes)
             lptr = C.cast(C.pointer(self._lh.s), C.c_void_p).value
         self.s = _Scene(self.R, (C.c_double * 3)(*self.O), M, N, Cc, K, _p(self.Po).value,
-                        _p(self.Pd).value, dt, tptr, sptr, lptr)
+                        _p(self.Pd).value, dt, tptr, sptr, lptr, rptr)
 
 
 def _views_arrays(views):

@@ -322,22 +322,28 @@ typedef struct {
     const void *table;       /* [M][N][C] FP32 or codes */
     const float *scales;     /* [M] for dtype 1, 2 */
     const lfo_lobes *lobes;  /* dtype 3 */
+    const int32_t *rowmap;   /* optional [M]: table/scale row holding origin row i (-1: absent) */
 } lfo_scene;
 
 static void lfo_fetch(const lfo_scene *S, uint32_t i, uint32_t j, double *v)
 {
-    size_t base = ((size_t)i * S->N + j) * S->C;
+    int64_t r = S->rowmap ? (int64_t)S->rowmap[i] : (int64_t)i;
+    if (S->dtype != 3 && r < 0) {
+        for (uint32_t c = 0; c < S->C; ++c) v[c] = NAN;
+        return;
+    }
+    size_t base = ((size_t)r * S->N + j) * S->C;
     switch (S->dtype) {
     case 0:
         for (uint32_t c = 0; c < S->C; ++c) v[c] = (double)((const float *)S->table)[base + c];
         break;
     case 1:
         for (uint32_t c = 0; c < S->C; ++c)
-            v[c] = (double)S->scales[i] * lfo_f16_decode(((const uint16_t *)S->table)[base + c]);
+            v[c] = (double)S->scales[r] * lfo_f16_decode(((const uint16_t *)S->table)[base + c]);
         break;
     case 2:
         for (uint32_t c = 0; c < S->C; ++c)
-            v[c] = (double)S->scales[i] * lfo_e4m3_decode(((const uint8_t *)S->table)[base + c]);
+            v[c] = (double)S->scales[r] * lfo_e4m3_decode(((const uint8_t *)S->table)[base + c]);
         break;
     default:
         lfo_lobe_texel(S->lobes, S->Po, S->Pd, i, j, v);

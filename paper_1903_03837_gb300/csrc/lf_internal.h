@@ -1,0 +1,59 @@
+// lf_internal.h -- structures shared by the host side of the C ABI and the
+// kernels of the light-field sampling library.
+#pragma once
+
+#include <stdint.h>
+
+#include "lumipath.h"
+
+namespace lfk {
+
+// Storage forms the kernels read (texel type x channel count).
+enum TexelKind { kF32C4 = 0, kF32C3 = 1, kF16C4 = 2, kE4M3C4 = 3 };
+
+// A view as the kernels read it (kernel-parameter space).
+struct ViewK {
+    float eye[3], right[3], up[3], fwd[3];
+    float tan_x, tan_y;
+    uint32_t width, height;
+    uint64_t out_offset;
+    uint32_t tiles_x, tiles_y;
+};
+
+// Sphere S: FP32 centre and radius for the ray/sphere step, the centre as a
+// hi/lo float pair and in FP64 for the unit hit vectors.
+struct SphereK {
+    float o32[3];
+    float r32;
+    float o_hi[3], o_lo[3];
+    double o64[3];
+};
+
+// One SF point set: p_i as hi/lo float4 pairs (w unused), n, n as float and
+// the reciprocal kernel radius 1/sqrt(4*pi/n).
+struct PointSetK {
+    const float4 *hi;
+    const float4 *lo;
+    uint32_t n;
+    float nf;
+    float inv_sigma;
+};
+
+}  // namespace lfk
+
+struct lf_table {
+    lf_table_desc desc;
+    int device;
+    int texel_kind;                  // lfk::TexelKind
+    uint32_t C;                      // logical channels (3 or 4)
+    const void *texels;              // [M][N][Cs]
+    const float *scales;             // [M] or NULL (F32)
+    void *owned_texels;              // non-NULL if the library owns the copy
+    float *owned_scales;
+    float4 *points;                  // [2M + 2N]: origins hi, lo, then directions hi, lo
+    uint32_t *scratch;               // [0] status word, [1] tile queue, [2] finished CTAs
+    lfk::SphereK sphere;
+    lfk::PointSetK po, pd;
+    lf_launch launch;
+    int sm_count;
+};

@@ -1,0 +1,60 @@
+// lf_kernels.h -- kernel parameter blocks and launchers (host <-> device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lf_internal.h"
+
+namespace lfk {
+
+constexpr int kSmallViews = 2;     // one view or a stereo pair per launch
+constexpr int kLargeViews = 64;    // batches are split into launches of <= 64 views
+constexpr int kMaxBlock = 256;     // threads per CTA (tile_w * tile_h)
+constexpr uint32_t kStripTiles = 4;
+
+struct RenderParamsBase {
+    SphereK sphere;
+    PointSetK po, pd;
+    const void *texels;            // [M][N][Cs]
+    const float *scales;           // [M] (F16 / E4M3)
+    uint32_t N;                    // texels per origin row
+    uint32_t C;                    // output / gradient channels (3 or 4)
+    float *out;                    // forward: [P][C]
+    int32_t *idx;                  // forward: [P][10] or NULL
+    const float *grad_out;         // backward: [P][C]
+    float *grad;                   // backward: [M][N][C]
+    uint32_t *status, *queue, *done;
+    uint32_t n_views, total_tiles;
+    uint32_t tile_w, tile_h, warp_w, order, persistent;
+};
+
+template <int MAXV>
+struct RenderParams : RenderParamsBase {
+    uint32_t tile_prefix[MAXV + 1];
+    ViewK views[MAXV];
+};
+
+cudaError_t launch_render_small(int kind, bool bwd, const RenderParams<kSmallViews> &p, unsigned grid,
+                                unsigned block, cudaStream_t st);
+cudaError_t launch_render_large(int kind, bool bwd, const RenderParams<kLargeViews> &p, unsigned grid,
+                                unsigned block, cudaStream_t st);
+int render_occupancy(int kind, bool bwd, bool large, unsigned block);
+
+// lf_table.cu
+cudaError_t launch_build_points(uint32_t n, float4 *hi, float4 *lo, cudaStream_t st);
+cudaError_t launch_pad_codes(const void *src, uint32_t M, uint32_t N, int bytes, void *dst, cudaStream_t st);
+cudaError_t launch_quantize(const float *src, uint32_t M, uint32_t N, uint32_t C, int dtype, void *codes,
+                            float *scales, cudaStream_t st);
+
+constexpr int kMaxLobes = 64;
+struct LobeParams {
+    uint32_t L, C;
+    uint64_t seed;
+    double ap[kMaxLobes][3], ad[kMaxLobes][3], kp[kMaxLobes], kd[kMaxLobes], col[kMaxLobes][4];
+};
+cudaError_t launch_fill_lobe(const LobeParams &P, const float4 *po_hi, const float4 *po_lo,
+                             const float4 *pd_hi, const float4 *pd_lo, uint32_t M, uint32_t N,
+                             float *out, cudaStream_t st);
+
+}  // namespace lfk

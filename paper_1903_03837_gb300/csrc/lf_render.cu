@@ -1,0 +1,269 @@
+// lf_render.cu -- forward render and backward scatter kernels of the
+// light-field sampling path (LumiPath, arXiv 1903.03837, Section 2).
+//
+// One thread per camera ray. A CTA renders a tile of tile_w x tile_h pixels of
+// one view; each warp covers a warp_w x (32/warp_w) sub-tile so that its rays
+// hit neighbouring SF cells and share texels in L1. Tiles of all views of a
+// call are numbered consecutively (view-major); a CTA either takes tile
+// blockIdx.x (static grid) or pulls tiles from a queue word (persistent grid
+// of SMs x occupancy CTAs; the last CTA to leave resets the queue, so the
+// launch is replayable, e.g. from a CUDA graph). Views live in the kernel's
+// parameter space (no device copy, graph friendly).
+#include <cuda_runtime.h>
+
+#include "lf_device.cuh"
+#include "lf_kernels.h"
+
+namespace lfk {
+
+__device__ __forceinline__ void tile_of(const RenderParamsBase &p, const ViewK *views,
+                                        const uint32_t *prefix, uint32_t nv, uint32_t t,
+                                        uint32_t &v, uint32_t &tx, uint32_t &ty)
+{
+    uint32_t lo = 0, hi = nv;          // largest v with prefix[v] <= t
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= t) lo = mid; else hi = mid;
+    }
+    v = lo;
+    uint32_t lt = t - prefix[v];
+    uint32_t tiles_x = views[v].tiles_x;
+    if (p.order == 0) {
+        tx = lt % tiles_x;
+        ty = lt / tiles_x;
+    } else {                           // strips of kStripTiles tile rows, column by column
+        uint32_t strip = lt / (tiles_x * kStripTiles);
+        uint32_t r = lt - strip * tiles_x * kStripTiles;
+        uint32_t hs = min(kStripTiles, views[v].tiles_y - strip * kStripTiles);
+        tx = r / hs;
+        ty = strip * kStripTiles + r % hs;
+    }
+}
+
+__device__ __forceinline__ void pixel_of(const RenderParamsBase &p, uint32_t tx, uint32_t ty,
+                                         uint32_t &px, uint32_t &py)
+{
+    uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t warp_h = 32u / p.warp_w;
+    uint32_t warps_x = p.tile_w / p.warp_w;
+    px = tx * p.tile_w + (warp % warps_x) * p.warp_w + lane % p.warp_w;
+    py = ty * p.tile_h + (warp / warps_x) * warp_h + lane / p.warp_w;
+}
+
+// Indices and normalised weights of one ray; false for a miss.
+__device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const ViewK &v, uint32_t px,
+                                            uint32_t py, int32_t io[5], int32_t jd[5], float wo[5],
+                                            float wd[5])
+{
+    float3 d = camera_dir(v, px, py);
+    float3 ho, hd;
+    if (!intersect_sphere(p.sphere, v.eye, d, ho, hd)) return false;
+    float d2o[5], d2d[5];
+    int co, cd;
+    knn5(p.po, p.sphere, ho, io, d2o, co, p.status);
+    knn5(p.pd, p.sphere, hd, jd, d2d, cd, p.status);
+    tent_weights(d2o, co, p.po.inv_sigma, wo);
+    tent_weights(d2d, cd, p.pd.inv_sigma, wd);
+    return true;
+}
+
+template <int DT>
+__device__ __forceinline__ void render_ray(const RenderParamsBase &p, const ViewK &v, uint32_t px,
+                                           uint32_t py)
+{
+    int32_t io[5], jd[5];
+    float wo[5], wd[5];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool hit = ray_samples(p, v, px, py, io, jd, wo, wd);
+    if (hit) {
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            int32_t i = max(io[a], 0);                 // a missing neighbour has weight 0
+            float s = wo[a];
+            if constexpr (DT == kF16C4 || DT == kE4M3C4) s *= __ldg(p.scales + i);
+            size_t row = (size_t)i * p.N;
+            float4 in = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+                float4 t = texel<DT>(p.texels, row + (uint32_t)max(jd[b], 0));
+                in.x = __fmaf_rn(wd[b], t.x, in.x);
+                in.y = __fmaf_rn(wd[b], t.y, in.y);
+                in.z = __fmaf_rn(wd[b], t.z, in.z);
+                in.w = __fmaf_rn(wd[b], t.w, in.w);
+            }
+            acc.x = __fmaf_rn(s, in.x, acc.x);
+            acc.y = __fmaf_rn(s, in.y, acc.y);
+            acc.z = __fmaf_rn(s, in.z, acc.z);
+            acc.w = __fmaf_rn(s, in.w, acc.w);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 5; ++a) io[a] = jd[a] = -1;
+    }
+    uint64_t pix = v.out_offset + (uint64_t)py * v.width + px;
+    if (p.C == 4) {
+        __stcs(reinterpret_cast<float4 *>(p.out) + pix, acc);
+    } else {
+        float *o = p.out + pix * 3;
+        __stcs(o, acc.x);
+        __stcs(o + 1, acc.y);
+        __stcs(o + 2, acc.z);
+    }
+    if (p.idx) {
+        int2 *q = reinterpret_cast<int2 *>(p.idx + pix * 10);
+        q[0] = make_int2(io[0], io[1]);
+        q[1] = make_int2(io[2], io[3]);
+        q[2] = make_int2(io[4], jd[0]);
+        q[3] = make_int2(jd[1], jd[2]);
+        q[4] = make_int2(jd[3], jd[4]);
+    }
+}
+
+// Sum of `val` over the lanes of this lane's group `grp` (lanes holding the
+// same texel key), delivered to the group's lowest lane. Every lane of the
+// warp calls this with the same `rounds` = largest group size.
+__device__ __forceinline__ float4 group_sum(float4 val, unsigned grp, int rounds)
+{
+    unsigned rest = grp & (grp - 1u);                 // members after the leader
+    float4 acc = val;
+    for (int r = 1; r < rounds; ++r) {
+        int src = rest ? (__ffs(rest) - 1) : (int)(threadIdx.x & 31);
+        float4 o;
+        o.x = __shfl_sync(0xffffffffu, val.x, src);
+        o.y = __shfl_sync(0xffffffffu, val.y, src);
+        o.z = __shfl_sync(0xffffffffu, val.z, src);
+        o.w = __shfl_sync(0xffffffffu, val.w, src);
+        if (rest) {
+            acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
+            rest &= rest - 1u;
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const ViewK *v, bool active,
+                                             uint32_t px, uint32_t py)
+{
+    int32_t io[5], jd[5];
+    float wo[5], wd[5];
+    bool hit = false;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) {
+        hit = ray_samples(p, *v, px, py, io, jd, wo, wd);
+        uint64_t pix = v->out_offset + (uint64_t)py * v->width + px;
+        if (p.C == 4) {
+            g = __ldg(reinterpret_cast<const float4 *>(p.grad_out) + pix);
+        } else {
+            const float *q = p.grad_out + pix * 3;
+            g = make_float4(__ldg(q), __ldg(q + 1), __ldg(q + 2), 0.f);
+        }
+    }
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            bool live = hit && io[a] >= 0 && jd[b] >= 0;
+            uint64_t key = live ? (uint64_t)io[a] * p.N + (uint64_t)jd[b] : ~0ull - lane;
+            float W = live ? wo[a] * wd[b] : 0.f;
+            float4 val = make_float4(W * g.x, W * g.y, W * g.z, W * g.w);
+            unsigned grp = __match_any_sync(0xffffffffu, key);
+            int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(grp));
+            float4 sum = group_sum(val, grp, rounds);
+            if (live && (__ffs(grp) - 1) == (int)lane) {
+                if (p.C == 4) {
+                    atomicAdd(reinterpret_cast<float4 *>(p.grad) + key, sum);
+                } else {
+                    float *q = p.grad + key * 3;
+                    atomicAdd(q, sum.x);
+                    atomicAdd(q + 1, sum.y);
+                    atomicAdd(q + 2, sum.z);
+                }
+            }
+        }
+    }
+}
+
+template <int DT, int MAXV, bool BWD>
+__global__ void __launch_bounds__(kMaxBlock) render_kernel(const __grid_constant__ RenderParams<MAXV> p)
+{
+    __shared__ uint32_t s_tile;
+    const uint32_t nv = p.n_views;
+    uint32_t t = p.persistent ? 0u : blockIdx.x;
+    for (;;) {
+        if (p.persistent) {
+            if (threadIdx.x == 0) s_tile = atomicAdd(p.queue, 1u);
+            __syncthreads();
+            t = s_tile;
+            __syncthreads();
+        }
+        if (t >= p.total_tiles) break;
+        uint32_t v, tx, ty, px, py;
+        tile_of(p, p.views, p.tile_prefix, nv, t, v, tx, ty);
+        pixel_of(p, tx, ty, px, py);
+        const ViewK &vw = p.views[v];
+        bool active = px < vw.width && py < vw.height;
+        if constexpr (BWD) {
+            backward_ray(p, &vw, active, px, py);
+        } else {
+            if (active) render_ray<DT>(p, vw, px, py);
+        }
+        if (!p.persistent) break;
+    }
+    if (p.persistent && threadIdx.x == 0) {
+        __threadfence();
+        uint32_t done = atomicAdd(p.done, 1u);
+        if (done == gridDim.x - 1) {                  // last CTA out: re-arm the queue
+            atomicExch(p.queue, 0u);
+            atomicExch(p.done, 0u);
+        }
+    }
+}
+
+template <int MAXV>
+static cudaError_t launch_t(int kind, bool bwd, const RenderParams<MAXV> &p, unsigned grid,
+                            unsigned block, cudaStream_t st)
+{
+    if (bwd) {
+        render_kernel<kF32C4, MAXV, true><<<grid, block, 0, st>>>(p);
+    } else {
+        switch (kind) {
+        case kF32C4: render_kernel<kF32C4, MAXV, false><<<grid, block, 0, st>>>(p); break;
+        case kF32C3: render_kernel<kF32C3, MAXV, false><<<grid, block, 0, st>>>(p); break;
+        case kF16C4: render_kernel<kF16C4, MAXV, false><<<grid, block, 0, st>>>(p); break;
+        default: render_kernel<kE4M3C4, MAXV, false><<<grid, block, 0, st>>>(p); break;
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <int MAXV>
+static int occupancy_t(int kind, bool bwd, unsigned block)
+{
+    int n = 0;
+    const void *f;
+    if (bwd) f = (const void *)render_kernel<kF32C4, MAXV, true>;
+    else if (kind == kF32C4) f = (const void *)render_kernel<kF32C4, MAXV, false>;
+    else if (kind == kF32C3) f = (const void *)render_kernel<kF32C3, MAXV, false>;
+    else if (kind == kF16C4) f = (const void *)render_kernel<kF16C4, MAXV, false>;
+    else f = (const void *)render_kernel<kE4M3C4, MAXV, false>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, (int)block, 0) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_render_small(int kind, bool bwd, const RenderParams<kSmallViews> &p, unsigned grid,
+                                unsigned block, cudaStream_t st)
+{
+    return launch_t<kSmallViews>(kind, bwd, p, grid, block, st);
+}
+cudaError_t launch_render_large(int kind, bool bwd, const RenderParams<kLargeViews> &p, unsigned grid,
+                                unsigned block, cudaStream_t st)
+{
+    return launch_t<kLargeViews>(kind, bwd, p, grid, block, st);
+}
+int render_occupancy(int kind, bool bwd, bool large, unsigned block)
+{
+    return large ? occupancy_t<kLargeViews>(kind, bwd, block) : occupancy_t<kSmallViews>(kind, bwd, block);
+}
+
+}  // namespace lfk

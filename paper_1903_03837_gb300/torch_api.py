@@ -1,0 +1,163 @@
+"""Tensor-level API over the C ABI: PyTorch supplies device memory and the
+current CUDA stream; the kernels of liblumipath.so do all of the work.
+
+* ``LightField``: a table on the GPU (create / render / backward / launch shape)
+* ``RenderFunction``: ``torch.autograd.Function`` whose backward is the
+  library's scatter-add kernel (for fitting a table to target views)
+* ``fill_lobe_table``: the synthetic lobe radiance field, filled on the GPU
+* ``quantize_table``: per-row FP16 / E4M3 storage of an FP32 table
+"""
+from __future__ import annotations
+
+from typing import Optional, Sequence, Tuple
+
+import torch
+
+from . import lumipath as lp
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _need_cuda(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def total_pixels(views: Sequence) -> int:
+    return max(int(v.out_offset) + int(v.width) * int(v.height) for v in views)
+
+
+class LightField:
+    """Light-field table L^(i,j) on the current CUDA device (Section 2).
+
+    radiance: [M,N,C] float32, or FP16/E4M3 codes ([M,N,C] int16/uint8) with
+    ``scales`` [M] float32. With ``borrow=True`` the library reads the tensor in
+    place (it must stay alive; its contents may change between renders).
+    """
+
+    def __init__(self, radiance: torch.Tensor, dtype: str = "f32", scales: Optional[torch.Tensor] = None,
+                 R: float = 1.0, O=(0.0, 0.0, 0.0), borrow: bool = False):
+        _need_cuda(radiance, "radiance")
+        if radiance.dim() != 3:
+            raise ValueError("radiance must be [M, N, C]")
+        M, N, Cc = (int(s) for s in radiance.shape)
+        ok = {"f32": (torch.float32,), "f16": (torch.int16, torch.float16),
+              "e4m3": (torch.uint8, torch.int8, torch.float8_e4m3fn)}[dtype]
+        if radiance.dtype not in ok:
+            raise ValueError(f"radiance dtype {radiance.dtype} does not match storage {dtype}")
+        if scales is not None:
+            _need_cuda(scales, "scales")
+        desc = lp.lf_table_desc()
+        desc.radius = float(R)
+        desc.center[:] = [float(o) for o in O]
+        desc.n_origins, desc.n_directions, desc.channels = M, N, Cc
+        desc.dtype = lp.DTYPES[dtype]
+        desc.flags = lp.LF_TABLE_BORROW if borrow else 0
+        desc.k_nearest = 5
+        self.M, self.N, self.C, self.dtype, self.R, self.O = M, N, Cc, dtype, float(R), tuple(O)
+        self._keep = (radiance, scales) if borrow else None
+        self.handle = lp.lf_create_table(desc, radiance.data_ptr(),
+                                         scales.data_ptr() if scales is not None else None, _stream())
+
+    # -- launch shape --------------------------------------------------------
+    def set_launch(self, tile_w=16, tile_h=16, warp_w=8, order=0, persistent=0, ctas_per_sm=0):
+        cfg = lp.lf_launch(tile_w, tile_h, warp_w, order, persistent, ctas_per_sm)
+        lp.lf_set_launch(self.handle, cfg)
+
+    def get_launch(self) -> dict:
+        return lp.lf_get_launch(self.handle).as_dict()
+
+    # -- rendering -------------------------------------------------------------
+    def render(self, views: Sequence, out: Optional[torch.Tensor] = None, with_idx: bool = False,
+               idx: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+        P = total_pixels(views)
+        if out is None:
+            out = torch.empty((P, self.C), dtype=torch.float32, device="cuda")
+        _need_cuda(out, "out")
+        if out.numel() < P * self.C or out.dtype != torch.float32:
+            raise ValueError("out must be float32 with at least P*C elements")
+        if with_idx and idx is None:
+            idx = torch.empty((P, 10), dtype=torch.int32, device="cuda")
+        if idx is not None:
+            _need_cuda(idx, "idx")
+            if idx.numel() < P * 10 or idx.dtype != torch.int32:
+                raise ValueError("idx must be int32 with at least P*10 elements")
+        vv = lp.make_views(views)
+        lp.lf_render(self.handle, vv, len(views), out.data_ptr(), idx.data_ptr() if idx is not None else None,
+                     _stream())
+        return out, idx
+
+    def render_backward(self, views: Sequence, grad_out: torch.Tensor,
+                        grad_table: Optional[torch.Tensor] = None) -> torch.Tensor:
+        _need_cuda(grad_out, "grad_out")
+        if grad_out.dtype != torch.float32 or grad_out.numel() < total_pixels(views) * self.C:
+            raise ValueError("grad_out must be float32 [P, C]")
+        if grad_table is None:
+            grad_table = torch.zeros((self.M, self.N, self.C), dtype=torch.float32, device="cuda")
+        _need_cuda(grad_table, "grad_table")
+        if grad_table.dtype != torch.float32 or grad_table.numel() != self.M * self.N * self.C:
+            raise ValueError("grad_table must be float32 [M, N, C]")
+        vv = lp.make_views(views)
+        lp.lf_render_backward(self.handle, vv, len(views), grad_out.data_ptr(), grad_table.data_ptr(), _stream())
+        return grad_table
+
+    def sync_status(self):
+        lp.lf_sync_status(self.handle, _stream())
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            lp.lf_destroy(h)
+        self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RenderFunction(torch.autograd.Function):
+    """image = render(table); d(loss)/d(table) by the library's backward kernel.
+
+    ``table`` must be the FP32 tensor that ``lf`` borrows (``borrow=True``)."""
+
+    @staticmethod
+    def forward(ctx, table: torch.Tensor, lf: LightField, views):
+        ctx.lf, ctx.views = lf, views
+        out, _ = lf.render(views)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad):
+        g = ctx.lf.render_backward(ctx.views, grad.contiguous())
+        return g, None, None
+
+
+def render(table: torch.Tensor, lf: LightField, views) -> torch.Tensor:
+    return RenderFunction.apply(table, lf, views)
+
+
+def fill_lobe_table(lobes, M: int, N: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """FP32 [M,N,C] lobe radiance field on the GPU (parameters from lf_inputs.draw_lobes)."""
+    if out is None:
+        out = torch.empty((M, N, lobes.C), dtype=torch.float32, device="cuda")
+    _need_cuda(out, "out")
+    lp.lf_fill_lobe_table(M, N, lobes.C, lobes.L, lobes.ap, lobes.ad, lobes.kp, lobes.kd, lobes.col,
+                          lobes.noise_seed, out.data_ptr(), _stream())
+    return out
+
+
+def quantize_table(T: torch.Tensor, dtype: str) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Per-row FP16 / E4M3 codes [M,N,4] (int16 holding binary16 bits, or uint8)
+    and scales [M] of an FP32 [M,N,C] table."""
+    _need_cuda(T, "T")
+    M, N, Cc = (int(s) for s in T.shape)
+    codes = torch.empty((M, N, 4), dtype=torch.int16 if dtype == "f16" else torch.uint8, device=T.device)
+    scales = torch.empty((M,), dtype=torch.float32, device=T.device)
+    lp.lf_quantize_table(T.data_ptr(), M, N, Cc, lp.DTYPES[dtype], codes.data_ptr(), scales.data_ptr(), _stream())
+    return codes, scales

@@ -1,0 +1,118 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+function include/lumipath.h declares, agrees with the binding on structure
+layouts, and rejects bad arguments with a status (never an abort) before any
+device work."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1903_03837_gb300 import build as B
+from paper_1903_03837_gb300 import lumipath as lp
+
+HEADER = os.path.join(B.INCLUDE, "lumipath.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(lf_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function():
+    lib = lp.lib()
+    names = declared_functions()
+    assert {"lf_create_table", "lf_render", "lf_render_backward", "lf_destroy"} <= set(names)
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (lf_[a-z0-9_]+)$", out, flags=re.M))
+    for n in names:
+        assert n in exported, n
+        assert getattr(lib, n) is not None
+
+
+def test_struct_layouts_match():
+    L = lp.lib()
+    assert L.lf_struct_size(0) == C.sizeof(lp.lf_table_desc) == 56
+    assert L.lf_struct_size(1) == C.sizeof(lp.lf_view) == 72
+    assert L.lf_struct_size(2) == C.sizeof(lp.lf_launch) == 24
+    assert L.lf_struct_size(7) == 0
+
+
+def test_built_for_sm_103a_only():
+    flags = " ".join(B.NVCC_FLAGS)
+    assert "arch=compute_103a,code=sm_103a" in flags
+    assert flags.count("-gencode") == 1
+
+
+def _desc(**kw):
+    d = lp.lf_table_desc()
+    d.radius = kw.get("radius", 1.0)
+    d.center[:] = kw.get("center", [0.0, 0.0, 0.0])
+    d.n_origins = kw.get("M", 64)
+    d.n_directions = kw.get("N", 32)
+    d.channels = kw.get("C", 4)
+    d.dtype = kw.get("dtype", 0)
+    d.flags = kw.get("flags", 0)
+    d.k_nearest = kw.get("k", 0)
+    return d
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(radius=0.0), lp.LF_ERR_INVALID_ARG),
+    (dict(radius=-1.0), lp.LF_ERR_INVALID_ARG),
+    (dict(radius=float("nan")), lp.LF_ERR_INVALID_ARG),
+    (dict(center=[0.0, float("inf"), 0.0]), lp.LF_ERR_INVALID_ARG),
+    (dict(M=0), lp.LF_ERR_INVALID_ARG),
+    (dict(N=0), lp.LF_ERR_INVALID_ARG),
+    (dict(M=(1 << 24) + 1), lp.LF_ERR_INVALID_ARG),
+    (dict(C=2), lp.LF_ERR_INVALID_ARG),
+    (dict(C=5), lp.LF_ERR_INVALID_ARG),
+    (dict(dtype=7), lp.LF_ERR_INVALID_ARG),
+    (dict(dtype=1), lp.LF_ERR_INVALID_ARG),          # F16 without scales
+    (dict(flags=0x80), lp.LF_ERR_INVALID_ARG),
+    (dict(k=9), lp.LF_ERR_UNSUPPORTED),
+])
+def test_create_table_rejects_bad_descriptions(kw, status):
+    h = C.c_void_p(123)
+    d = _desc(**kw)
+    s = lp.lib().lf_create_table(C.byref(d), C.c_void_p(0x1000), None, None, C.byref(h))
+    assert s == status
+    assert h.value is None
+    assert lp.lf_last_error() != ""
+
+
+def test_null_arguments_are_errors_not_crashes():
+    L = lp.lib()
+    h = C.c_void_p()
+    assert L.lf_create_table(None, C.c_void_p(0x1000), None, None, C.byref(h)) == lp.LF_ERR_INVALID_ARG
+    d = _desc()
+    assert L.lf_create_table(C.byref(d), None, None, None, C.byref(h)) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_create_table(C.byref(d), C.c_void_p(0x1000), None, None, None) == lp.LF_ERR_INVALID_ARG
+    views = lp.make_views([])
+    assert L.lf_render(None, views, 0, C.c_void_p(0x1000), None, None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_render_backward(None, views, 0, None, None, None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_set_launch(None, None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_sync_status(None, None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_quantize_table(None, 4, 4, 4, 1, None, None, None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_quantize_table(C.c_void_p(16), 4, 4, 4, 0, C.c_void_p(16), C.c_void_p(16), None) \
+        == lp.LF_ERR_INVALID_ARG
+    assert L.lf_fill_lobe_table(4, 4, 4, 65, None, None, None, None, None, 0, C.c_void_p(16), None) \
+        == lp.LF_ERR_INVALID_ARG
+    L.lf_destroy(None)
+
+
+def test_error_message_is_thread_local():
+    import threading
+    L = lp.lib()
+    h = C.c_void_p()
+    d = _desc(C=9)
+    L.lf_create_table(C.byref(d), C.c_void_p(0x1000), None, None, C.byref(h))
+    mine = lp.lf_last_error()
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(lp.lf_last_error()))
+    t.start()
+    t.join()
+    assert "channels" in mine and seen == [""]
