@@ -176,6 +176,35 @@ lf_status lf_fill_lobe_table(uint32_t M, uint32_t N, uint32_t C, uint32_t L,
                              const double *kd, const double *col, uint64_t noise_seed,
                              float *out_dev, void *stream);
 
+/* Largest M + N that lf_render_noalloc accepts. */
+#define LF_NOALLOC_MAX_POINTS 278528u
+
+/* Render without allocating any device memory. The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc -- a process whose
+ * device memory is already fully reserved by another runtime's pool (an
+ * allocation would fail), or a frame-paced loop that must not call
+ * cudaMalloc/cudaFree because they synchronise the device and take unbounded
+ * time. Instead of a table object, the call takes the table description and
+ * the caller's device arrays directly (radiance [M][N][C] FP32 with C in
+ * {3,4}, or FP16/E4M3 codes [M][N][4] with row_scales_dev [M]; views, out_dev
+ * and idx_dev as for lf_render; launch may be NULL for the default shape). It
+ * writes the same image and indices as lf_create_table + lf_render.
+ * The SF point caches and the status/queue words live in one fixed device
+ * array inside the library (32 B per point for up to LF_NOALLOC_MAX_POINTS
+ * points, about 8.5 MiB), which every GPU that loads the library keeps until
+ * the process exits. Each call rebuilds that content on `stream` and leaves
+ * the last call's contents behind; calls that overlap on the GPU (other
+ * streams or threads) race on it. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, once per device, with that
+ * device current); make that first call before any stream capture.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: LF_ERR_INVALID_ARG (including M + N > LF_NOALLOC_MAX_POINTS, with a
+ * message saying so), LF_ERR_UNSUPPORTED, LF_ERR_CUDA. */
+lf_status lf_render_noalloc(const lf_table_desc *desc, const void *radiance_dev,
+                            const float *row_scales_dev, const lf_view *views_host,
+                            uint32_t n_views, const lf_launch *launch, float *out_dev,
+                            int32_t *idx_dev, void *stream);
+
 /* Number of SMs of the current device (0 without one) and the library
  * version string. */
 int lf_device_sm_count(void);

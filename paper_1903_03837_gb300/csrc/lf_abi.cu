@@ -188,6 +188,10 @@ size_t code_bytes(int dtype) { return dtype == LF_DTYPE_F32 ? 4 : (dtype == LF_D
 
 }  // namespace
 
+namespace lfk {
+void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+}  // namespace lfk
+
 extern "C" {
 
 const char *lf_last_error(void) { return g_err.c_str(); }

@@ -57,4 +57,7 @@ cudaError_t launch_fill_lobe(const LobeParams &P, const float4 *po_hi, const flo
                              const float4 *pd_hi, const float4 *pd_lo, uint32_t M, uint32_t N,
                              float *out, cudaStream_t st);
 
+// Sets the calling thread's lf_last_error() message (lf_abi.cu).
+void set_last_error(const char *msg);
+
 }  // namespace lfk

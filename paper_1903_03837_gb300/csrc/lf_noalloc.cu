@@ -1,0 +1,224 @@
+// lf_noalloc.cu -- lf_render_noalloc: a render that allocates no device memory.
+//
+// lf_create_table allocates the SF point caches, a copy of the table and a
+// few status/queue words with cudaMalloc. Some callers cannot do that: a
+// process whose device memory is already fully reserved by another runtime's
+// memory pool (cudaMalloc would fail), or a frame-paced render loop that must
+// not call cudaMalloc/cudaFree because they synchronise the device and have
+// unbounded latency. For them this entry point keeps everything it needs
+// beyond the caller's inputs and outputs in one file-scope device array of
+// fixed size, g_lf_noalloc_scratch, which every GPU that loads the library
+// holds until the process exits.
+//
+// Layout of the array: the hi/lo point caches of both SF sets (M + N points,
+// 32 B each) followed by 256 B of words (status, tile queue, finished CTAs).
+// Every call rebuilds the point caches and clears the words on its stream, so
+// the array only ever holds the last call's contents; calls that overlap on
+// the GPU (different streams, or another thread) race on it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "lf_kernels.h"
+#include "lumipath.h"
+
+namespace {
+
+constexpr uint64_t kNoAllocMaxPoints = LF_NOALLOC_MAX_POINTS;     // M + N
+constexpr uint64_t kWordsFloat4 = 16;                                // 256 B of words
+
+static __device__ __align__(256) float4 g_lf_noalloc_scratch[2 * kNoAllocMaxPoints + kWordsFloat4];
+
+std::mutex g_addr_mu;
+void *g_addr[256];          // device address of the array, per device ordinal
+
+lf_status na_fail(lf_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    lfk::set_last_error(buf);
+    return s;
+}
+
+// Host code must not use g_lf_noalloc_scratch directly: on the host it names a
+// stand-in object, not device memory. Look up its device address once per
+// device, with that device current.
+lf_status scratch_address(int dev, float4 **out)
+{
+    if (dev < 0 || dev >= 256) return na_fail(LF_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_addr_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_lf_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return na_fail(LF_ERR_CUDA, "cudaGetSymbolAddress of the no-allocation scratch: %s",
+                           cudaGetErrorString(e));
+        g_addr[dev] = p;
+    }
+    *out = (float4 *)g_addr[dev];
+    return LF_OK;
+}
+
+template <int MAXV>
+lf_status launch_views(const lfk::RenderParamsBase &base, const lf_launch &L, int kind, int sm_count,
+                       const lf_view *views, uint32_t nv, cudaStream_t st)
+{
+    static thread_local lfk::RenderParams<MAXV> p;
+    static_cast<lfk::RenderParamsBase &>(p) = base;
+    uint64_t tiles = 0;
+    for (uint32_t v = 0; v < nv; ++v) {
+        lfk::ViewK &k = p.views[v];
+        const lf_view &w = views[v];
+        for (int i = 0; i < 3; ++i) {
+            k.eye[i] = w.eye[i];
+            k.right[i] = w.right[i];
+            k.up[i] = w.up[i];
+            k.fwd[i] = w.forward[i];
+        }
+        k.tan_x = w.tan_half_x;
+        k.tan_y = w.tan_half_y;
+        k.width = w.width;
+        k.height = w.height;
+        k.out_offset = w.out_offset;
+        k.tiles_x = (w.width + L.tile_w - 1) / L.tile_w;
+        k.tiles_y = (w.height + L.tile_h - 1) / L.tile_h;
+        p.tile_prefix[v] = (uint32_t)tiles;
+        tiles += (uint64_t)k.tiles_x * k.tiles_y;
+    }
+    if (tiles >= (1ull << 31)) return na_fail(LF_ERR_INVALID_ARG, "too many tiles in one launch");
+    p.tile_prefix[nv] = (uint32_t)tiles;
+    p.n_views = nv;
+    p.total_tiles = (uint32_t)tiles;
+    unsigned block = L.tile_w * L.tile_h;
+    unsigned grid = (unsigned)tiles;
+    if (L.persistent) {
+        int per_sm = L.ctas_per_sm ? (int)L.ctas_per_sm
+                                   : lfk::render_occupancy(kind, false, MAXV != lfk::kSmallViews, block);
+        uint64_t g = (uint64_t)sm_count * (uint64_t)per_sm;
+        grid = (unsigned)(g < tiles ? g : tiles);
+    }
+    if (grid == 0) return LF_OK;
+    cudaError_t e;
+    if constexpr (MAXV == lfk::kSmallViews)
+        e = lfk::launch_render_small(kind, false, p, grid, block, st);
+    else
+        e = lfk::launch_render_large(kind, false, p, grid, block, st);
+    if (e != cudaSuccess) return na_fail(LF_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
+    return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, const float *row_scales_dev,
+                            const lf_view *views, uint32_t n_views, const lf_launch *launch,
+                            float *out_dev, int32_t *idx_dev, void *stream)
+{
+    lfk::set_last_error("");
+    if (!d || !radiance_dev || !views || !out_dev) return na_fail(LF_ERR_INVALID_ARG, "NULL argument");
+    if (!(std::isfinite(d->radius) && d->radius > 0.0))
+        return na_fail(LF_ERR_INVALID_ARG, "radius must be finite and > 0");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(d->center[k])) return na_fail(LF_ERR_INVALID_ARG, "center must be finite");
+    const uint32_t M = d->n_origins, N = d->n_directions, C = d->channels;
+    if (M == 0 || N == 0) return na_fail(LF_ERR_INVALID_ARG, "point counts must be >= 1");
+    if ((uint64_t)M + N > kNoAllocMaxPoints)
+        return na_fail(LF_ERR_INVALID_ARG,
+                       "M + N = %llu exceeds the no-allocation scratch limit of %llu points",
+                       (unsigned long long)M + N, (unsigned long long)kNoAllocMaxPoints);
+    if (C != 3 && C != 4) return na_fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4");
+    if (d->dtype != LF_DTYPE_F32 && d->dtype != LF_DTYPE_F16 && d->dtype != LF_DTYPE_E4M3)
+        return na_fail(LF_ERR_INVALID_ARG, "unknown dtype %d", d->dtype);
+    const bool quant = d->dtype != LF_DTYPE_F32;
+    if (quant && (C != 4 || !row_scales_dev))
+        return na_fail(LF_ERR_INVALID_ARG, "F16/E4M3 tables need 4 channels and row scales here");
+    if (d->k_nearest != 0 && d->k_nearest != 5)
+        return na_fail(LF_ERR_UNSUPPORTED, "only 5 neighbours per hit are built");
+    if (n_views == 0 || n_views > 65536) return na_fail(LF_ERR_INVALID_ARG, "n_views must be in [1, 65536]");
+    for (uint32_t v = 0; v < n_views; ++v) {
+        const lf_view &w = views[v];
+        if (w.width == 0 || w.height == 0 || w.width > 65536 || w.height > 65536)
+            return na_fail(LF_ERR_INVALID_ARG, "view %u: size out of range", v);
+        bool fin = std::isfinite(w.tan_half_x) && std::isfinite(w.tan_half_y);
+        for (int k = 0; k < 3; ++k)
+            fin = fin && std::isfinite(w.eye[k]) && std::isfinite(w.right[k]) && std::isfinite(w.up[k]) &&
+                  std::isfinite(w.forward[k]);
+        if (!fin) return na_fail(LF_ERR_INVALID_ARG, "view %u: non-finite camera", v);
+        uint64_t end = w.out_offset + (uint64_t)w.width * w.height;
+        if (end < w.out_offset || end > (1ull << 40)) return na_fail(LF_ERR_INVALID_ARG, "view %u: output overflows", v);
+    }
+    lf_launch L;
+    if (launch) {
+        L = *launch;
+        uint32_t ww = L.warp_w;
+        bool ok = (ww == 1 || ww == 2 || ww == 4 || ww == 8 || ww == 16 || ww == 32) && L.tile_w && L.tile_h &&
+                  L.tile_w % ww == 0 && L.tile_h % (32 / ww) == 0 && L.tile_w * L.tile_h <= (uint32_t)lfk::kMaxBlock &&
+                  L.order <= 1 && L.persistent <= 1 && L.ctas_per_sm <= 64;
+        if (!ok) return na_fail(LF_ERR_INVALID_ARG, "inconsistent launch shape");
+    } else {
+        L = {16, 16, 8, 0, 0, 0};
+    }
+
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return na_fail(LF_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    float4 *base = nullptr;
+    lf_status s = scratch_address(dev, &base);
+    if (s != LF_OK) return s;
+    int sm_count = 0;
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    float4 *po_hi = base, *po_lo = base + M, *pd_hi = base + 2 * (uint64_t)M, *pd_lo = pd_hi + N;
+    uint32_t *words = reinterpret_cast<uint32_t *>(base + 2 * kNoAllocMaxPoints);
+    e = cudaMemsetAsync(words, 0, kWordsFloat4 * sizeof(float4), st);
+    if (e == cudaSuccess) e = lfk::launch_build_points(M, po_hi, po_lo, st);
+    if (e == cudaSuccess) e = lfk::launch_build_points(N, pd_hi, pd_lo, st);
+    if (e != cudaSuccess) return na_fail(LF_ERR_CUDA, "scratch set-up: %s", cudaGetErrorString(e));
+
+    lfk::RenderParamsBase b;
+    memset(&b, 0, sizeof b);
+    b.sphere.r32 = (float)d->radius;
+    for (int k = 0; k < 3; ++k) {
+        b.sphere.o32[k] = (float)d->center[k];
+        b.sphere.o_hi[k] = (float)d->center[k];
+        b.sphere.o_lo[k] = (float)(d->center[k] - (double)b.sphere.o_hi[k]);
+        b.sphere.o64[k] = d->center[k];
+    }
+    const double four_pi = 12.566370614359172953850573533118;
+    b.po = {po_hi, po_lo, M, (float)M, (float)(1.0 / std::sqrt(four_pi / (double)M))};
+    b.pd = {pd_hi, pd_lo, N, (float)N, (float)(1.0 / std::sqrt(four_pi / (double)N))};
+    b.texels = radiance_dev;
+    b.scales = quant ? row_scales_dev : nullptr;
+    b.N = N;
+    b.C = C;
+    b.out = out_dev;
+    b.idx = idx_dev;
+    b.status = words;
+    b.queue = words + 1;
+    b.done = words + 2;
+    b.tile_w = L.tile_w;
+    b.tile_h = L.tile_h;
+    b.warp_w = L.warp_w;
+    b.order = L.order;
+    b.persistent = L.persistent;
+    int kind = !quant ? (C == 4 ? lfk::kF32C4 : lfk::kF32C3) : (d->dtype == LF_DTYPE_F16 ? lfk::kF16C4 : lfk::kE4M3C4);
+    if (n_views <= (uint32_t)lfk::kSmallViews)
+        return launch_views<lfk::kSmallViews>(b, L, kind, sm_count, views, n_views, st);
+    for (uint32_t v0 = 0; v0 < n_views; v0 += lfk::kLargeViews) {
+        uint32_t nv = n_views - v0 < (uint32_t)lfk::kLargeViews ? n_views - v0 : (uint32_t)lfk::kLargeViews;
+        s = launch_views<lfk::kLargeViews>(b, L, kind, sm_count, views + v0, nv, st);
+        if (s != LF_OK) return s;
+    }
+    return LF_OK;
+}
+
+}  // extern "C"

@@ -78,6 +78,8 @@ def lib():
                 "lf_device_sm_count": (C.c_int, []),
                 "lf_version": (C.c_char_p, []),
                 "lf_struct_size": (C.c_size_t, [C.c_int]),
+                "lf_render_noalloc": (st, [C.POINTER(lf_table_desc), vp, vp, C.POINTER(lf_view), u32,
+                                           C.POINTER(lf_launch), vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -172,6 +174,17 @@ def lf_fill_lobe_table(M: int, N: int, Cc: int, L: int, ap, ad, kp, kd, col, noi
     ptrs = [a.ctypes.data_as(C.c_void_p) if a.size else None for a in arrs]
     _check(lib().lf_fill_lobe_table(M, N, Cc, L, *ptrs, C.c_uint64(noise_seed & (2**64 - 1)),
                                     C.c_void_p(out_ptr), C.c_void_p(stream or None)))
+
+
+def lf_render_noalloc(desc: lf_table_desc, radiance_ptr: int, scales_ptr: Optional[int], views,
+                      n_views: int, launch: Optional[lf_launch], out_ptr: int, idx_ptr: Optional[int],
+                      stream: int = 0):
+    """Render straight from the caller's arrays; the library allocates nothing
+    (for callers that cannot call cudaMalloc; see include/lumipath.h)."""
+    _check(lib().lf_render_noalloc(C.byref(desc), C.c_void_p(radiance_ptr), C.c_void_p(scales_ptr or None),
+                                   views, n_views, C.byref(launch) if launch is not None else None,
+                                   C.c_void_p(out_ptr), C.c_void_p(idx_ptr or None),
+                                   C.c_void_p(stream or None)))
 
 
 def lf_device_sm_count() -> int:
