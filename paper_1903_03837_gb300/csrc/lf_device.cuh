@@ -46,11 +46,6 @@ constexpr float kInvLog2Phi2 = 0.72021234840458929f;    // 1 / log2(Phi^2)
 constexpr float kSqrt5Pi = 7.0248147310407731f;          // sqrt(5)*pi
 constexpr float kInv2Pi = 0.15915494309189535f;
 
-// Certification margins of the FP32 ranking (see knn5): relative gap needed
-// between consecutive keys for the order to be exact, by slot-bit count.
-__device__ __forceinline__ float tau_for_bits(int bits) { return __int_as_float((127 + bits - 21) << 23); }
-constexpr float kTauAbs = 3.637978807091713e-12f;      // 2^-38
-
 // ---------------------------------------------------------------------------
 // Camera ray and sphere intersection: IEEE FP32, fixed order, no contraction.
 // ---------------------------------------------------------------------------
@@ -181,17 +176,19 @@ __device__ __forceinline__ double dist2_fp64(const PointSetK &P, int32_t i, cons
 // Inverse SF mapping, extended to the 5 nearest points (Section 2).
 //
 // Candidate sources:
-//   FULL   n <= 128: every point (slot = index, 7 slot bits).
+//   FULL   n <= 128: every point (slot = index).
 //   POLE   the continuous index (n(1-z)-1)/2 of the hit lies within 16 of a
-//          pole: the 64 points nearest that pole (slot = offset, 6 bits).
+//          pole: the 64 points nearest that pole (slot = offset).
 //   WINDOW otherwise: the 4x4 lattice cells around floor(u, v), where (u, v)
 //          are the hit's coordinates in the local Fibonacci basis of zone k
-//          (slot = 4*(du+1) + (dv+1), 4 bits).
-// Each candidate's squared distance becomes a 32-bit key (float bits with the
-// low slot bits replaced by the slot); the 6 smallest keys are kept sorted.
-// The FP32 order is accepted when every consecutive gap among those 6 exceeds
-// the combined rounding and packing error; otherwise the same candidates are
-// ranked again in FP64 by (distance, index).
+//          (slot = 4*(du+1) + (dv+1)).
+// Tier 1 ranks every candidate by an FP32 squared distance from the hi parts
+// only (key = float bits with the low bits replaced by the slot) and keeps the
+// 7 smallest keys. With the rigorous error bound e1 of that distance, the true
+// 5 nearest lie among the tier-1 top 6 when the 5th key's upper bound is below
+// the 7th key's lower bound. Tier 2 recomputes those 6 in double-float, sorts
+// them and accepts the order when every consecutive gap exceeds the tier-2
+// error. Anything uncertain is ranked again in FP64 by (distance, index).
 // ---------------------------------------------------------------------------
 #define LF_CS(a, b)                          \
     {                                        \
@@ -200,10 +197,10 @@ __device__ __forceinline__ double dist2_fp64(const PointSetK &P, int32_t i, cons
         k[a] = lo_;                          \
     }
 
-__device__ __forceinline__ void select6_of16(uint32_t k[16])
+// Batcher odd-even merge sort of 16 keys, pruned to the comparators that
+// reach outputs 0..6 (the 7 smallest, sorted; 54 comparators).
+__device__ __forceinline__ void select7_of16(uint32_t k[16])
 {
-    // Batcher odd-even merge sort of 16 keys, pruned to the comparators that
-    // reach outputs 0..5 (54 comparators).
     LF_CS(0, 1) LF_CS(2, 3) LF_CS(0, 2) LF_CS(1, 3) LF_CS(1, 2) LF_CS(4, 5) LF_CS(6, 7)
     LF_CS(4, 6) LF_CS(5, 7) LF_CS(5, 6) LF_CS(0, 4) LF_CS(2, 6) LF_CS(2, 4) LF_CS(1, 5)
     LF_CS(3, 7) LF_CS(3, 5) LF_CS(1, 2) LF_CS(3, 4) LF_CS(5, 6) LF_CS(8, 9) LF_CS(10, 11)
@@ -215,28 +212,21 @@ __device__ __forceinline__ void select6_of16(uint32_t k[16])
     LF_CS(5, 6)
 }
 
-__device__ __forceinline__ void insert6(uint32_t s[6], uint32_t key)
+// Optimal 12-comparator network sorting 6 keys.
+__device__ __forceinline__ void sort6(uint32_t k[6])
+{
+    LF_CS(1, 2) LF_CS(4, 5) LF_CS(0, 2) LF_CS(3, 5) LF_CS(0, 1) LF_CS(3, 4) LF_CS(1, 4)
+    LF_CS(0, 3) LF_CS(2, 5) LF_CS(1, 3) LF_CS(2, 4) LF_CS(2, 3)
+}
+
+__device__ __forceinline__ void insert7(uint32_t s[7], uint32_t key)
 {
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
+    for (int m = 0; m < 7; ++m) {
         uint32_t lo = min(key, s[m]);
         key = max(key, s[m]);
         s[m] = lo;
     }
-}
-
-// FP64 insertion by (d2, index); idx/dd hold `cnt` sorted entries (cnt <= 5).
-__device__ __forceinline__ void insert5_exact(int32_t idx[5], double dd[5], int &cnt, int32_t i, double d)
-{
-    if (cnt == 5 && !(d < dd[4] || (d == dd[4] && i < idx[4]))) return;
-    int s = cnt < 5 ? cnt++ : 4;
-    while (s > 0 && (d < dd[s - 1] || (d == dd[s - 1] && i < idx[s - 1]))) {
-        dd[s] = dd[s - 1];
-        idx[s] = idx[s - 1];
-        --s;
-    }
-    dd[s] = d;
-    idx[s] = i;
 }
 
 struct Window {
@@ -265,97 +255,186 @@ __device__ __forceinline__ int32_t window_index(const Window &w, int slot)
     return w.base + ((slot >> 2) - 1) * w.F0 + ((slot & 3) - 1) * w.F1;
 }
 
-// Result: idx[0..cnt) in (distance, index) order and their FP32 squared
-// distances d2 (recomputed in double-float). cnt = min(5, n).
-__device__ __forceinline__ void knn5(const PointSetK &P, const SphereK &S, float3 h, int32_t idx[5],
-                                  float d2[5], int &cnt, uint32_t *status)
+// Candidate source of one query (see above).
+struct Source {
+    Window w;
+    int32_t scan_base, scan_cnt;   // scan_cnt == 0: window
+    int bits;                      // tier-1 slot bits
+};
+
+__device__ __forceinline__ Source candidate_source(const PointSetK &P, float3 qh)
+{
+    const int32_t n = (int32_t)P.n;
+    Source s;
+    s.w = {0, 0, 0};
+    s.scan_base = 0;
+    s.scan_cnt = 0;
+    s.bits = 4;
+    if (n <= 128) {
+        s.scan_cnt = n;
+        s.bits = 7;
+    } else {
+        float icn = (P.nf * (1.0f - qh.z) - 1.0f) * 0.5f;
+        float ics = (P.nf * (1.0f + qh.z) - 1.0f) * 0.5f;
+        if (icn < 16.0f) {
+            s.scan_cnt = 64;
+            s.bits = 6;
+        } else if (ics < 16.0f) {
+            s.scan_base = n - 64;
+            s.scan_cnt = 64;
+            s.bits = 6;
+        } else {
+            s.w = lattice_window(P, qh);
+        }
+    }
+    return s;
+}
+
+__device__ __forceinline__ int32_t source_index(const Source &s, int slot)
+{
+    return s.scan_cnt ? s.scan_base + slot : window_index(s.w, slot);
+}
+
+// Tier-1 squared distance from the hi parts only.
+__device__ __forceinline__ float dist2_hi(const PointSetK &P, int32_t i, float3 qh)
+{
+    float4 a = __ldg(P.hi + i);
+    float dx = __fsub_rn(qh.x, a.x), dy = __fsub_rn(qh.y, a.y), dz = __fsub_rn(qh.z, a.z);
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+// Bound of |dist2_hi - d^2| (hi parts within 2^-24 of q and p per component,
+// one rounding per subtraction, three roundings in the sum of squares).
+__device__ __forceinline__ float tier1_err(float d2)
+{
+    return __fmaf_rn(0x1p-21f, d2, __fmaf_rn(0x1p-21f, sqrtf(d2), 0x1p-43f));
+}
+
+struct Top5 {
+    int32_t i[5];
+    float d2[5];
+    int cnt;
+};
+
+// Exact ranking in FP64 over the same candidates (rare: an uncertain order).
+__device__ __noinline__ Top5 knn5_fp64(const PointSetK P, const SphereK S, float3 h, const Source src,
+                                       float3 qh, float3 ql)
+{
+    double q[3];
+    unit_hit_fp64(S, h, q);
+    int32_t idx[5];
+    double dd[5];
+    int cnt = 0;
+    const int32_t n = (int32_t)P.n;
+    const int total = src.scan_cnt ? src.scan_cnt : 16;
+    for (int s = 0; s < total; ++s) {
+        int32_t i = source_index(src, s);
+        if (i < 0 || i >= n) continue;
+        double d = dist2_fp64(P, i, q);
+        if (cnt == 5 && !(d < dd[4] || (d == dd[4] && i < idx[4]))) continue;
+        int m = cnt < 5 ? cnt++ : 4;
+        while (m > 0 && (d < dd[m - 1] || (d == dd[m - 1] && i < idx[m - 1]))) {
+            dd[m] = dd[m - 1];
+            idx[m] = idx[m - 1];
+            --m;
+        }
+        dd[m] = d;
+        idx[m] = i;
+    }
+    Top5 r;
+    for (int m = 0; m < 5; ++m) {
+        r.i[m] = m < cnt ? idx[m] : -1;
+        r.d2[m] = m < cnt ? dist2_df(P, idx[m], qh, ql) : 0.0f;
+    }
+    r.cnt = cnt;
+    return r;
+}
+
+// The 5 nearest points of the unit hit (qh + ql) in (distance, index) order,
+// with their double-float squared distances. cnt = min(5, n).
+__device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float3 h, uint32_t *status)
 {
     float3 qh, ql;
     unit_hit_df(S, h, qh, ql);
     const int32_t n = (int32_t)P.n;
-    int src;            // 0 window, 1 scan
-    int32_t scan_base = 0, scan_cnt = 0;
-    int bits;
-    Window w{0, 0, 0};
-    if (n <= 128) {
-        src = 1; scan_cnt = n; bits = 7;
-    } else {
-        float icn = (P.nf * (1.0f - qh.z) - 1.0f) * 0.5f;
-        float ics = (P.nf * (1.0f + qh.z) - 1.0f) * 0.5f;
-        if (icn < 16.0f) { src = 1; scan_cnt = 64; bits = 6; }
-        else if (ics < 16.0f) { src = 1; scan_base = n - 64; scan_cnt = 64; bits = 6; }
-        else { src = 0; bits = 4; w = lattice_window(P, qh); }
-    }
-    const uint32_t mask = (1u << bits) - 1u;
-    uint32_t s6[6];
-    if (src == 0) {
+    const Source src = candidate_source(P, qh);
+    const uint32_t mask1 = (1u << src.bits) - 1u;
+    constexpr uint32_t kNone = 0xffffffffu;
+
+    // Tier 1: the 7 smallest FP32 keys.
+    uint32_t s7[7];
+    if (src.scan_cnt == 0) {
         uint32_t k[16];
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
-            int32_t i = window_index(w, s);
-            bool ok = (i >= 0) & (i < n);
-            float dd = ok ? dist2_df(P, i, qh, ql) : 0.0f;
-            k[s] = ok ? ((__float_as_uint(dd) & ~mask) | (uint32_t)s) : 0xffffffffu;
+            int32_t i = window_index(src.w, s);
+            bool ok = (uint32_t)i < (uint32_t)n;
+            float dd = dist2_hi(P, ok ? i : 0, qh);
+            k[s] = ok ? ((__float_as_uint(dd) & ~15u) | (uint32_t)s) : kNone;
         }
-        select6_of16(k);
+        select7_of16(k);
 #pragma unroll
-        for (int m = 0; m < 6; ++m) s6[m] = k[m];
+        for (int m = 0; m < 7; ++m) s7[m] = k[m];
     } else {
 #pragma unroll
-        for (int m = 0; m < 6; ++m) s6[m] = 0xffffffffu;
-        for (int s = 0; s < scan_cnt; ++s) {
-            float dd = dist2_df(P, scan_base + s, qh, ql);
-            insert6(s6, (__float_as_uint(dd) & ~mask) | (uint32_t)s);
-        }
+        for (int m = 0; m < 7; ++m) s7[m] = kNone;
+        for (int s = 0; s < src.scan_cnt; ++s)
+            insert7(s7, (__float_as_uint(dist2_hi(P, src.scan_base + s, qh)) & ~mask1) | (uint32_t)s);
     }
-    // Certification of the FP32 order (including the 5th/6th boundary).
-    const float tau = tau_for_bits(bits);
+
+    // Membership: 5th upper bound below the 7th lower bound.
     bool exact = true;
+    if (s7[6] != kNone) {
+        float a = __uint_as_float(s7[4] & ~mask1), b = __uint_as_float(s7[6] & ~mask1);
+        float pack = __uint_as_float(s7[4] | mask1) - a;
+        exact = (b - tier1_err(b)) > (a + pack + tier1_err(a + pack));
+    }
+
+    // Tier 2: double-float distances of the top 6, sorted; 3 slot bits.
+    uint32_t k6[6];
+    int32_t id6[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        bool ok = s7[m] != kNone;
+        int32_t i = ok ? source_index(src, (int)(s7[m] & mask1)) : 0;
+        id6[m] = i;
+        float dd = dist2_df(P, i, qh, ql);
+        k6[m] = ok ? ((__float_as_uint(dd) & ~7u) | (uint32_t)m) : kNone;
+    }
+    sort6(k6);
+    // Order among the 5 and the 5th/6th boundary at tier-2 precision.
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        if (s6[m + 1] != 0xffffffffu) {
-            float a = __uint_as_float(s6[m] & ~mask), b = __uint_as_float(s6[m + 1] & ~mask);
-            exact &= (b - a) > __fmaf_rn(tau, b, kTauAbs);
+        if (k6[m + 1] != kNone) {
+            float a = __uint_as_float(k6[m] & ~7u), b = __uint_as_float(k6[m + 1] & ~7u);
+            exact &= (b - a) > __fmaf_rn(0x1p-18f, b, 0x1p-40f);
         }
     }
-    cnt = 0;
+    Top5 r;
     if (exact) {
+        r.cnt = 0;
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            if (s6[m] != 0xffffffffu) {
-                int slot = (int)(s6[m] & mask);
-                idx[m] = src == 0 ? window_index(w, slot) : scan_base + slot;
-                cnt = m + 1;
-            } else {
-                idx[m] = -1;
-            }
+            bool ok = k6[m] != kNone;
+            int sl = (int)(k6[m] & 7u);
+            int32_t i = id6[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c) i = (sl == c) ? id6[c] : i;
+            r.i[m] = ok ? i : -1;
+            r.d2[m] = ok ? __uint_as_float(k6[m] & ~7u) : 0.0f;
+            r.cnt += ok ? 1 : 0;
         }
     } else {
-        double q[3], dd[5];
-        unit_hit_fp64(S, h, q);
-        if (src == 0) {
-            for (int s = 0; s < 16; ++s) {
-                int32_t i = window_index(w, s);
-                if (i >= 0 && i < n) insert5_exact(idx, dd, cnt, i, dist2_fp64(P, i, q));
-            }
-        } else {
-            for (int s = 0; s < scan_cnt; ++s)
-                insert5_exact(idx, dd, cnt, scan_base + s, dist2_fp64(P, scan_base + s, q));
-        }
-        for (int m = cnt; m < 5; ++m) idx[m] = -1;
+        r = knn5_fp64(P, S, h, src, qh, ql);
     }
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        if (m < cnt) {
-            if ((uint32_t)idx[m] >= (uint32_t)n) {   // impossible by construction; recorded, never trapped
-                atomicOr(status, 1u);
-                idx[m] = 0;
-            }
-            d2[m] = dist2_df(P, idx[m], qh, ql);
-        } else {
-            d2[m] = 0.0f;
+        if (m < r.cnt && (uint32_t)r.i[m] >= (uint32_t)n) {   // impossible by construction; recorded, never trapped
+            atomicOr(status, 1u);
+            r.i[m] = 0;
         }
     }
+    return r;
 }
 
 // Tent weights of one set, normalised to sum 1 (nearest takes all if none is
@@ -365,12 +444,13 @@ __device__ __forceinline__ void tent_weights(const float d2[5], int cnt, float i
     float S = 0.0f;
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        float v = m < cnt ? fmaxf(0.0f, 1.0f - sqrtf(d2[m]) * inv_sigma) : 0.0f;
+        float d = d2[m] * rsqrtf(fmaxf(d2[m], 1e-37f));
+        float v = m < cnt ? fmaxf(0.0f, 1.0f - d * inv_sigma) : 0.0f;
         w[m] = v;
         S += v;
     }
     if (S > 0.0f) {
-        float r = 1.0f / S;
+        float r = __frcp_rn(S);
 #pragma unroll
         for (int m = 0; m < 5; ++m) w[m] *= r;
     } else {

@@ -14,6 +14,10 @@
 #include "lf_device.cuh"
 #include "lf_kernels.h"
 
+#ifndef LF_MIN_BLOCKS
+#define LF_MIN_BLOCKS 3
+#endif
+
 namespace lfk {
 
 __device__ __forceinline__ void tile_of(const RenderParamsBase &p, const ViewK *views,
@@ -58,12 +62,32 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
     float3 d = camera_dir(v, px, py);
     float3 ho, hd;
     if (!intersect_sphere(p.sphere, v.eye, d, ho, hd)) return false;
-    float d2o[5], d2d[5];
-    int co, cd;
-    knn5(p.po, p.sphere, ho, io, d2o, co, p.status);
-    knn5(p.pd, p.sphere, hd, jd, d2d, cd, p.status);
-    tent_weights(d2o, co, p.po.inv_sigma, wo);
-    tent_weights(d2d, cd, p.pd.inv_sigma, wd);
+    // One copy of the index step serves both sets (instruction-cache footprint).
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        PointSetK P;
+        P.hi = s ? p.pd.hi : p.po.hi;
+        P.lo = s ? p.pd.lo : p.po.lo;
+        P.n = s ? p.pd.n : p.po.n;
+        P.nf = s ? p.pd.nf : p.po.nf;
+        P.inv_sigma = s ? p.pd.inv_sigma : p.po.inv_sigma;
+        Top5 r = knn5(P, p.sphere, s ? hd : ho, p.status);
+        float w[5];
+        tent_weights(r.d2, r.cnt, P.inv_sigma, w);
+        if (s == 0) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                io[m] = r.i[m];
+                wo[m] = w[m];
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                jd[m] = r.i[m];
+                wd[m] = w[m];
+            }
+        }
+    }
     return true;
 }
 
@@ -185,7 +209,7 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
 }
 
 template <int DT, int MAXV, bool BWD>
-__global__ void __launch_bounds__(kMaxBlock) render_kernel(const __grid_constant__ RenderParams<MAXV> p)
+__global__ void __launch_bounds__(kMaxBlock, LF_MIN_BLOCKS) render_kernel(const __grid_constant__ RenderParams<MAXV> p)
 {
     __shared__ uint32_t s_tile;
     const uint32_t nv = p.n_views;
