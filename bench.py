@@ -135,7 +135,7 @@ def run_ours(args, rank: int, world: int):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev_index = torch.cuda.current_device()
-    cfg = lf_inputs.config_large()
+    cfg = lf_inputs.config_large() if args.workload == "large" else lf_inputs.config_precision()
     lob = cfg.lobes()
     M, N = cfg.M, cfg.N
     t0 = time.time()
@@ -149,12 +149,21 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     setup_s = time.time() - t0
 
-    frames_total = cfg.extra["frames"]
-    my_frames = [(rank * (args.steps + args.warmup) + k) % frames_total for k in range(args.steps + args.warmup)]
-    frame_views = {f: lf_inputs.orbit_frame(f) for f in set(my_frames)}
+    if args.workload == "large":
+        frames_total = cfg.extra["frames"]
+        my_frames = [(rank * (args.steps + args.warmup) + k) % frames_total
+                     for k in range(args.steps + args.warmup)]
+        frame_views = {f: lf_inputs.orbit_frame(f) for f in set(my_frames)}
+    else:
+        my_frames = [0] * (args.steps + args.warmup)
+        frame_views = {0: cfg.views}
     rays = cfg.rays
-    launch = autotune.best_launch(tables[args.dtype], [frame_views[my_frames[0]]], key=f"large-{args.dtype}",
-                                  quick=args.quick_tune)
+    if args.launch:
+        tw, th, ww, order, pers = (int(x) for x in args.launch.split(","))
+        launch = dict(tile_w=tw, tile_h=th, warp_w=ww, order=order, persistent=pers, ctas_per_sm=0)
+    else:
+        launch = autotune.best_launch(tables[args.dtype], [frame_views[my_frames[0]]],
+                                      key=f"{args.workload}-{args.dtype}", quick=args.quick_tune)
     for t in tables.values():
         t.set_launch(**launch)
 
@@ -198,7 +207,7 @@ def run_ours(args, rank: int, world: int):
         total_ms, per_ms, nbytes = timed(args.dtype)
     clocks = clk.summary()
     variants = {}
-    for dt in ("f16", "f32"):
+    for dt in (("f16", "f32") if not args.no_variants else ()):
         if dt == args.dtype:
             continue
         tm, pm, nb = timed(dt)
@@ -249,7 +258,9 @@ def run_ours(args, rank: int, world: int):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(cfg), "table_storage": args.dtype,
+        "config": {"workload": workload_name(cfg) if args.workload == "large" else
+                   f"precision: {cfg.M:,} x {cfg.N:,} RGBA table, one 1920x1080 view at 2.5R",
+                   "table_storage": args.dtype,
                    "rays_per_step": rays, "hit_fraction": hit_frac,
                    "l2": "inputs larger than L2: 4 GiB table, 265 MB image per step, orbit frame changes every step",
                    "launch": launch, "parallelism": f"replicas x{world} (views sharded, no collective)",
@@ -266,12 +277,69 @@ def run_ours(args, rank: int, world: int):
         "variants": variants,
         "psnr_vs_f32_table_db": psnr_vs_f32,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if not args.no_variants:
+        for t in tables.values():
+            t.close()
+        del T32, codes, tables, outs
+        torch.cuda.empty_cache()
+        line["fit"] = run_fit_steps(args)
+        tables = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "large":
         line["cpu_baseline"], psnr64 = cpu_baseline(cfg, frame_views[f0], gpu_images, args)
         line["psnr_vs_fp64_db"] = psnr64
     for t in tables.values():
         t.close()
     return line
+
+
+def run_fit_steps(args):
+    """Differentiation workload: 16,384 x 512 RGB FP32 table, 32 target views of
+    512x512; one step = render (forward kernel) + MSE + backward scatter kernel +
+    Adam on the FP32 table. Times the steps and the backward launches alone."""
+    import torch
+    from paper_1903_03837_gb300 import torch_api as api
+    cfg = lf_inputs.config_differentiation()
+    train = lf_inputs.pack_offsets(cfg.views[:cfg.extra["n_train"]])
+    rays = lf_inputs.total_pixels(train)
+    gt = api.fill_lobe_table(cfg.lobes(), cfg.M, cfg.N)
+    lf_gt = api.LightField(gt, "f32", borrow=True)
+    target, _ = lf_gt.render(train)
+    table = torch.zeros_like(gt, requires_grad=True)
+    lf = api.LightField(table.detach(), "f32", borrow=True)
+    opt = torch.optim.Adam([table], lr=cfg.extra["lr"])
+    st = torch.cuda.current_stream()
+    bwd_ms = []
+
+    def step(timed):
+        opt.zero_grad(set_to_none=False)
+        img, _ = lf.render(train)
+        g = (2.0 / img.numel()) * (img - target)
+        if timed:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+        lf.render_backward(train, g, table.grad)
+        if timed:
+            b.record(st)
+            bwd_ms.append((a, b))
+        opt.step()
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step(True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    bms = sum(a.elapsed_time(b) for a, b in bwd_ms) / len(bwd_ms)
+    lf.close()
+    lf_gt.close()
+    return {"workload": f"differentiation: {cfg.M:,} x {cfg.N:,} RGB FP32 table, {len(train)} views 512x512 "
+                        f"({rays:,} rays), Adam lr 1e-2",
+            "ms_per_fit_step": ms, "fit_steps_per_s": 1e3 / ms,
+            "backward_ms": bms, "backward_grays_s": rays / (bms * 1e-3) / 1e9,
+            "fwd_bwd_adam_grays_s": rays / (ms * 1e-3) / 1e9}
 
 
 def cpu_baseline(cfg, views, gpu_images, args):
@@ -349,6 +417,10 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick-tune", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--launch", default="", help="tile_w,tile_h,warp_w,order,persistent (skips the autotuner)")
+    ap.add_argument("--workload", default="large", choices=["large", "precision"],
+                    help="precision: 65,536 x 1,024 table, one 1920x1080 view (small profiling case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

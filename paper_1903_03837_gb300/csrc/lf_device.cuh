@@ -179,9 +179,8 @@ __device__ __forceinline__ double dist2_fp64(const PointSetK &P, int32_t i, cons
 //   FULL   n <= 128: every point (slot = index).
 //   POLE   the continuous index (n(1-z)-1)/2 of the hit lies within 16 of a
 //          pole: the 64 points nearest that pole (slot = offset).
-//   WINDOW otherwise: the 4x4 lattice cells around floor(u, v), where (u, v)
-//          are the hit's coordinates in the local Fibonacci basis of zone k
-//          (slot = 4*(du+1) + (dv+1)).
+//   WINDOW otherwise: 12 lattice corners around round(u, v) (below), where
+//          (u, v) are the hit's coordinates in the local Fibonacci basis of zone k.
 // Tier 1 ranks every candidate by an FP32 squared distance from the hi parts
 // only (key = float bits with the low bits replaced by the slot) and keeps the
 // 7 smallest keys. With the rigorous error bound e1 of that distance, the true
@@ -229,8 +228,16 @@ __device__ __forceinline__ void insert7(uint32_t s[7], uint32_t key)
     }
 }
 
+// Lattice window: (u, v) rounded to the nearest cell corner (ru, rv); the
+// candidates are the 3x3 corners around it plus three corners on the side of
+// the sign quadrant of (u - ru, v - rv). A brute-force study over n = 256 ...
+// 262,144 (3.3 M queries, (u, v) perturbed by +-2e-3, zone number flipped by
+// +-1) found the true 5 nearest always inside these 12 corners away from the
+// poles.
 struct Window {
     int32_t base, F0, F1;
+    int32_t ext[3];          // index offsets of the three quadrant corners
+    bool interior;           // every candidate index lies in [0, n)
 };
 
 __device__ __forceinline__ Window lattice_window(const PointSetK &P, float3 qh)
@@ -246,13 +253,34 @@ __device__ __forceinline__ Window lattice_window(const PointSetK &P, float3 qh)
     float sg = (k & 1) ? -1.0f : 1.0f;
     float u = sg * __fmaf_rn(-(float)F1, t, e1 * ic);
     float v = sg * __fmaf_rn((float)F0, t, -e0 * ic);
-    int32_t u0 = __float2int_rd(u), v0 = __float2int_rd(v);
-    return {u0 * F0 + v0 * F1, F0, F1};
+    float ru = rintf(u), rv = rintf(v);
+    bool pu = u >= ru, pv = v >= rv;
+    Window w;
+    w.base = (int32_t)ru * F0 + (int32_t)rv * F1;
+    w.F0 = F0;
+    w.F1 = F1;
+    // quadrant corners (du, dv): (-,-): (-2,0) (-1,-2) (-2,1); (-,+): (-2,1) (0,2) (1,2);
+    //                            (+,-): (-1,-2) (0,-2) (2,-1); (+,+): (1,2) (2,-1) (2,0)
+    if (!pu && !pv) {
+        w.ext[0] = -2 * F0; w.ext[1] = -F0 - 2 * F1; w.ext[2] = -2 * F0 + F1;
+    } else if (!pu) {
+        w.ext[0] = -2 * F0 + F1; w.ext[1] = 2 * F1; w.ext[2] = F0 + 2 * F1;
+    } else if (!pv) {
+        w.ext[0] = -F0 - 2 * F1; w.ext[1] = -2 * F1; w.ext[2] = 2 * F0 - F1;
+    } else {
+        w.ext[0] = F0 + 2 * F1; w.ext[1] = 2 * F0 - F1; w.ext[2] = 2 * F0;
+    }
+    const int32_t reach = 2 * (F0 + F1);
+    w.interior = (w.base - reach >= 0) && (w.base + reach < (int32_t)P.n);
+    return w;
 }
+
+constexpr int kWindow = 12;
 
 __device__ __forceinline__ int32_t window_index(const Window &w, int slot)
 {
-    return w.base + ((slot >> 2) - 1) * w.F0 + ((slot & 3) - 1) * w.F1;
+    if (slot < 9) return w.base + (slot / 3 - 1) * w.F0 + (slot % 3 - 1) * w.F1;
+    return w.base + w.ext[slot - 9];
 }
 
 // Candidate source of one query (see above).
@@ -266,7 +294,9 @@ __device__ __forceinline__ Source candidate_source(const PointSetK &P, float3 qh
 {
     const int32_t n = (int32_t)P.n;
     Source s;
-    s.w = {0, 0, 0};
+    s.w.base = s.w.F0 = s.w.F1 = 0;
+    s.w.ext[0] = s.w.ext[1] = s.w.ext[2] = 0;
+    s.w.interior = false;
     s.scan_base = 0;
     s.scan_cnt = 0;
     s.bits = 4;
@@ -307,7 +337,8 @@ __device__ __forceinline__ float dist2_hi(const PointSetK &P, int32_t i, float3 
 // one rounding per subtraction, three roundings in the sum of squares).
 __device__ __forceinline__ float tier1_err(float d2)
 {
-    return __fmaf_rn(0x1p-21f, d2, __fmaf_rn(0x1p-21f, sqrtf(d2), 0x1p-43f));
+    float d = d2 * rsqrtf(fmaxf(d2, 0x1p-100f));          // sqrt(d2) to a few ulps
+    return __fmaf_rn(0x1p-21f, d2, __fmaf_rn(0x1p-20f, d, 0x1p-42f));
 }
 
 struct Top5 {
@@ -326,7 +357,7 @@ __device__ __noinline__ Top5 knn5_fp64(const PointSetK P, const SphereK S, float
     double dd[5];
     int cnt = 0;
     const int32_t n = (int32_t)P.n;
-    const int total = src.scan_cnt ? src.scan_cnt : 16;
+    const int total = src.scan_cnt ? src.scan_cnt : kWindow;
     for (int s = 0; s < total; ++s) {
         int32_t i = source_index(src, s);
         if (i < 0 || i >= n) continue;
@@ -365,13 +396,23 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
     uint32_t s7[7];
     if (src.scan_cnt == 0) {
         uint32_t k[16];
+        if (src.w.interior) {
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            int32_t i = window_index(src.w, s);
-            bool ok = (uint32_t)i < (uint32_t)n;
-            float dd = dist2_hi(P, ok ? i : 0, qh);
-            k[s] = ok ? ((__float_as_uint(dd) & ~15u) | (uint32_t)s) : kNone;
+            for (int s = 0; s < kWindow; ++s) {
+                float dd = dist2_hi(P, window_index(src.w, s), qh);
+                k[s] = (__float_as_uint(dd) & ~15u) | (uint32_t)s;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < kWindow; ++s) {
+                int32_t i = window_index(src.w, s);
+                bool ok = (uint32_t)i < (uint32_t)n;
+                float dd = dist2_hi(P, ok ? i : 0, qh);
+                k[s] = ok ? ((__float_as_uint(dd) & ~15u) | (uint32_t)s) : kNone;
+            }
         }
+#pragma unroll
+        for (int s = kWindow; s < 16; ++s) k[s] = kNone;
         select7_of16(k);
 #pragma unroll
         for (int m = 0; m < 7; ++m) s7[m] = k[m];

@@ -1,0 +1,195 @@
+"""Parity at the workloads' full sizes, in the launch configuration the benchmark
+uses, on sampled pixels the oracle computes one by one.
+
+The GPU fills its own table (lf_fill_lobe_table, FP64 lobe field rounded to
+FP32) and quantises it on the GPU; the oracle evaluates the same lobe field
+itself for the rows the sampled pixels touch, quantises those rows with its own
+codec, and renders the sampled pixels by brute force. Indices must agree
+bit-exactly and colours within 1e-5; quantised tables are also compared with
+the FP64 field (PSNR)."""
+import numpy as np
+import pytest
+
+import lf_inputs
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ATOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_03837_gb300 import torch_api
+    return torch_api
+
+
+def oracle_expected(cfg, lobes, views, pix, dtypes):
+    """Oracle outputs of the sampled pixels for each storage type, plus the
+    FP64 lobe-field reference, the indices and the hit mask."""
+    ref, idx, hits = oracle.render_pixels(
+        oracle.Scene(cfg.M, cfg.N, cfg.C, "lobe", lobes=lobes), views, pix)
+    rows = np.unique(idx[:, :5][idx[:, :5] >= 0])
+    T_rows = oracle.lobe_table(lobes, cfg.M, cfg.N, rows=rows)
+    want = {}
+    for dt in dtypes:
+        if dt == "f32":
+            sc = oracle.Scene(cfg.M, cfg.N, cfg.C, "f32", T_rows, rows=rows)
+        else:
+            codes, s = oracle.quantize_rows(T_rows, dt)
+            sc = oracle.Scene(cfg.M, cfg.N, cfg.C, dt, codes, s, rows=rows)
+        want[dt] = oracle.render_pixels(sc, views, pix)[0]
+    return ref, idx, idx[:, 0] >= 0, want, rows, T_rows
+
+
+def gpu_tables(api, cfg, lobes, dtypes):
+    T32 = api.fill_lobe_table(lobes, cfg.M, cfg.N)
+    out = {}
+    for dt in dtypes:
+        if dt == "f32":
+            out[dt] = (api.LightField(T32, "f32", borrow=True), None)
+        else:
+            c, s = api.quantize_table(T32, dt)
+            out[dt] = (api.LightField(c, dt, s, borrow=True), (c, s))
+    return T32, out
+
+
+def check(name, got_out, got_idx, want_out, want_idx):
+    mism = np.any(got_idx != want_idx, axis=1)
+    assert mism.sum() == 0, f"{name}: {mism.sum()} sampled rays with different indices"
+    err = float(np.abs(got_out.astype(np.float64) - want_out).max())
+    assert err <= ATOL, f"{name}: max abs error {err:.3g}"
+
+
+@pytest.mark.parametrize("frame", [0, 77])
+def test_large_config_sampled(api, frame):
+    from paper_1903_03837_gb300 import autotune
+    cfg = lf_inputs.config_large(frame=frame)
+    lobes = cfg.lobes()
+    views = cfg.views
+    dtypes = ("e4m3", "f16", "f32")
+    T32, tabs = gpu_tables(api, cfg, lobes, dtypes)
+    launch = autotune.best_launch(tabs["e4m3"][0], [views], key="large-e4m3")
+    pix = lf_inputs.sample_pixels(views, 1500, seed=frame)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    ref, want_idx, hit, want, rows, T_rows = oracle_expected(cfg, lobes, views, pix, dtypes)
+    assert hit.sum() > 300
+    # the GPU fill equals the oracle's field on the touched rows
+    g_rows = T32[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.mean(g_rows != T_rows) < 1e-5
+    psnr = {}
+    for dt in dtypes:
+        lf = tabs[dt][0]
+        lf.set_launch(**launch)
+        out, idx = lf.render(views, with_idx=True)
+        lf.sync_status()
+        o, i = out.cpu().numpy()[offs], idx.cpu().numpy()[offs]
+        check(f"large/{dt}", o, i, want[dt], want_idx)
+        psnr[dt] = oracle.psnr(ref, o.astype(np.float64), hit)
+        lf.close()
+    assert psnr["f32"] > 120 and psnr["f16"] > 80 and psnr["e4m3"] > 45, psnr
+    assert psnr["f32"] > psnr["f16"] > psnr["e4m3"]
+
+
+def test_precision_config_sampled(api):
+    cfg = lf_inputs.config_precision()
+    lobes = cfg.lobes()
+    views = cfg.views
+    dtypes = ("f32", "f16", "e4m3")
+    T32, tabs = gpu_tables(api, cfg, lobes, dtypes)
+    pix = lf_inputs.sample_pixels(views, 3000, seed=2)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    ref, want_idx, hit, want, rows, T_rows = oracle_expected(cfg, lobes, views, pix, dtypes)
+    psnr = {}
+    for dt in dtypes:
+        out, idx = tabs[dt][0].render(views, with_idx=True)
+        o, i = out.cpu().numpy()[offs], idx.cpu().numpy()[offs]
+        check(f"precision/{dt}", o, i, want[dt], want_idx)
+        psnr[dt] = oracle.psnr(ref, o.astype(np.float64), hit)
+        tabs[dt][0].close()
+    assert psnr["f32"] > psnr["f16"] > psnr["e4m3"] > 40, psnr
+
+
+def test_batching_config_graph_replay(api):
+    from paper_1903_03837_gb300 import autotune
+    cfg = lf_inputs.config_batching()
+    lobes = cfg.lobes()
+    views = cfg.views
+    assert len(views) == 64
+    T32, tabs = gpu_tables(api, cfg, lobes, ("f16",))
+    lf = tabs["f16"][0]
+    launch = autotune.best_launch(lf, [views], key="batching-f16")
+    P = cfg.rays
+    direct, idx = lf.render(views, with_idx=True)
+    direct = direct.clone()
+    # one persistent launch of all 64 views, captured in a CUDA graph and replayed
+    lf.set_launch(**dict(launch, persistent=1))
+    out = torch.empty((P, 4), device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        lf.render(views, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        lf.render(views, out=out)
+    for _ in range(3):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, direct)
+    pix = lf_inputs.sample_pixels(views, 3000, seed=3)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    ref, want_idx, hit, want, rows, T_rows = oracle_expected(cfg, lobes, views, pix, ("f16",))
+    check("batching/f16", direct.cpu().numpy()[offs], idx.cpu().numpy()[offs], want["f16"], want_idx)
+    lf.close()
+
+
+def test_differentiation_config_fit(api):
+    """Ground truth 16,384 x 512 RGB FP32; 32 target views 512x512; zero-initialised
+    FP32 table fitted by Adam (lr 1e-2, 500 steps) through the backward kernel."""
+    from paper_1903_03837_gb300.torch_api import render
+    cfg = lf_inputs.config_differentiation()
+    lobes = cfg.lobes()
+    ntr = cfg.extra["n_train"]
+    train = lf_inputs.pack_offsets(cfg.views[:ntr])
+    held = lf_inputs.pack_offsets(cfg.views[ntr:])
+    gt = api.fill_lobe_table(lobes, cfg.M, cfg.N)
+    lf_gt = api.LightField(gt, "f32", borrow=True)
+    # sampled parity of the ground-truth render
+    pix = lf_inputs.sample_pixels(train, 2000, seed=4)
+    offs = lf_inputs.pixel_offsets(train, pix)
+    ref, want_idx, hit, want, rows, T_rows = oracle_expected(cfg, lobes, train, pix, ("f32",))
+    target, idx = lf_gt.render(train, with_idx=True)
+    check("differentiation/gt", target.cpu().numpy()[offs], idx.cpu().numpy()[offs], want["f32"], want_idx)
+    held_target, held_idx = lf_gt.render(held, with_idx=True)
+    held_hit = held_idx[:, 0] >= 0
+
+    table = torch.zeros_like(gt, requires_grad=True)
+    lf = api.LightField(table.detach(), "f32", borrow=True)
+    opt = torch.optim.Adam([table], lr=cfg.extra["lr"], betas=(0.9, 0.999), eps=1e-8)
+    first = None
+    for step in range(cfg.extra["steps"]):
+        opt.zero_grad(set_to_none=False)
+        img = render(table, lf, train)
+        loss = ((img - target) ** 2).mean()
+        loss.backward()
+        opt.step()
+        if first is None:
+            first = float(loss.detach())
+    last = float(loss.detach())
+    pred, _ = lf.render(held)
+
+    def psnr(a, b, m):
+        mse = float(((a[m] - b[m]) ** 2).mean())
+        return 10 * np.log10(float(b[m].max()) ** 2 / mse)
+    p_fit = psnr(pred, held_target, held_hit)
+    p_zero = psnr(torch.zeros_like(pred), held_target, held_hit)
+    print(f"fit: loss {first:.4g} -> {last:.4g}; held-out PSNR {p_fit:.2f} dB (zero table {p_zero:.2f} dB)")
+    assert last < 0.02 * first, (first, last)
+    assert p_fit > p_zero, (p_fit, p_zero)
+    lf.close()
+    lf_gt.close()

@@ -308,3 +308,36 @@ def test_status_word_clean_and_cpu_tensors_rejected(api):
     lf.close()
     with pytest.raises(ValueError):
         api.LightField(torch.zeros((4, 4, 4)), "f32")
+
+
+@pytest.mark.parametrize("M,N", [(1024, 256), (16384, 512), (262144, 4096)])
+def test_index_step_stress_against_kdtree(api, M, N):
+    """Millions of rays from random cameras: every index set equals the library
+    k-d tree's 5 nearest (the oracle's brute force is pinned to it)."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(M + 1)
+    views = lf_inputs.pack_offsets([lf_inputs.look_at(rng.uniform(1.3, 4.0) * lf_inputs._random_dir(rng),
+                                                      0.2 * rng.standard_normal(3), 640, 640)
+                                    for _ in range(8)])
+    codes = torch.zeros((M, N, 4), dtype=torch.uint8, device="cuda")
+    lf = api.LightField(codes, "e4m3", torch.ones((M,), device="cuda"), borrow=True)
+    _, idx = lf.render(views, with_idx=True)
+    lf.sync_status()
+    idx = idx.cpu().numpy()
+    lf.close()
+    pix = lf_inputs.pixel_list(views)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    idx = idx[offs]
+    hit = idx[:, 0] >= 0
+    qo = np.zeros((len(pix), 3))
+    qd = np.zeros((len(pix), 3))
+    # unit hit vectors from the oracle's FP32 ray / sphere step, for the hit rays
+    sel = np.nonzero(hit)[0]
+    sub = sel[:: max(1, len(sel) // 400000)]
+    for k in sub:
+        _, _, _, _, qo[k], qd[k] = oracle.trace_pixel(1.0, (0, 0, 0), views[pix[k, 0]], pix[k, 1], pix[k, 2])
+    for P, q, cols in ((oracle.sf_points(M), qo, slice(0, 5)), (oracle.sf_points(N), qd, slice(5, 10))):
+        _, nn = cKDTree(P).query(q[sub], k=5)
+        bad = np.any(np.sort(idx[sub][:, cols], axis=1) != np.sort(nn, axis=1), axis=1)
+        assert bad.sum() == 0, f"{bad.sum()} of {len(sub)} index sets differ from the k-d tree"
+    assert len(sub) > 100000
