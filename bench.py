@@ -131,7 +131,7 @@ def run_ours(args, rank: int, world: int):
     import torch
     from paper_1903_03837_gb300 import torch_api as api
     from paper_1903_03837_gb300 import lumipath as lp
-    from paper_1903_03837_gb300 import autotune
+    from paper_1903_03837_gb300 import autotune, replicas
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev_index = torch.cuda.current_device()
@@ -151,8 +151,7 @@ def run_ours(args, rank: int, world: int):
 
     if args.workload == "large":
         frames_total = cfg.extra["frames"]
-        my_frames = [(rank * (args.steps + args.warmup) + k) % frames_total
-                     for k in range(args.steps + args.warmup)]
+        my_frames = replicas.frames_for_rank(rank, world, args.steps + args.warmup, frames_total)
         frame_views = {f: lf_inputs.orbit_frame(f) for f in set(my_frames)}
     else:
         my_frames = [0] * (args.steps + args.warmup)
@@ -196,9 +195,7 @@ def run_ours(args, rank: int, world: int):
         per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
         total_ms = ev[0].elapsed_time(ev[-1])
         if world > 1:
-            tt = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(tt)
+            total_ms = replicas.reduce_max(total_ms)
             torch.distributed.barrier()
         nbytes = sum(algorithmic_bytes(hits[my_frames[args.warmup + k]], rays, dtype) for k in range(args.steps))
         return total_ms, per, nbytes
@@ -243,9 +240,7 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t_e2e
     if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt)
+        e2e_s = replicas.reduce_max(e2e_s)
 
     peak, peak_kind = measured_peaks()
     avg_launch_s = sum(per_ms) / len(per_ms) * 1e-3
