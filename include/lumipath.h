@@ -84,13 +84,14 @@ typedef struct lf_view {
 } lf_view;
 
 /* Launch shape of the render and backward kernels (chosen by the autotuner).
- * block = tile_w * tile_h threads; one thread per ray; each warp covers a
- * warp_w x (32/warp_w) pixel sub-tile. */
+ * block = tile_w * tile_h threads (at most 256); one thread per ray; each warp
+ * covers a warp_w x (32/warp_w) pixel sub-tile. tile_w and tile_h are powers
+ * of two. */
 typedef struct lf_launch {
-    uint32_t tile_w;           /* pixels per CTA tile in x; multiple of warp_w */
-    uint32_t tile_h;           /* pixels per CTA tile in y; multiple of 32/warp_w */
+    uint32_t tile_w;           /* pixels per CTA tile in x; power of two, multiple of warp_w */
+    uint32_t tile_h;           /* pixels per CTA tile in y; power of two, multiple of 32/warp_w */
     uint32_t warp_w;           /* 1, 2, 4, 8, 16 or 32 */
-    uint32_t order;            /* 0: tiles in raster order per view; 1: Z-order */
+    uint32_t order;            /* 0: tiles in raster order per view; 1: strips of 4 tile rows, column by column */
     uint32_t persistent;       /* 0: one CTA per tile; 1: CTAs pull tiles from a queue */
     uint32_t ctas_per_sm;      /* persistent grid = SMs * ctas_per_sm (0: occupancy) */
 } lf_launch;

@@ -60,7 +60,9 @@ lf_status check_launch(const lf_launch *c)
     if (!(ww == 1 || ww == 2 || ww == 4 || ww == 8 || ww == 16 || ww == 32))
         return fail(LF_ERR_INVALID_ARG, "warp_w must be 1, 2, 4, 8, 16 or 32 (got %u)", ww);
     uint32_t wh = 32 / ww;
-    if (c->tile_w == 0 || c->tile_h == 0 || c->tile_w % ww || c->tile_h % wh)
+    if (c->tile_w == 0 || c->tile_h == 0 || (c->tile_w & (c->tile_w - 1)) || (c->tile_h & (c->tile_h - 1)))
+        return fail(LF_ERR_INVALID_ARG, "tile %ux%u: both sides must be powers of two", c->tile_w, c->tile_h);
+    if (c->tile_w % ww || c->tile_h % wh)
         return fail(LF_ERR_INVALID_ARG, "tile %ux%u is not a whole number of %ux%u warp tiles",
                     c->tile_w, c->tile_h, ww, wh);
     if (c->tile_w * c->tile_h > (uint32_t)lfk::kMaxBlock)
@@ -173,6 +175,9 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
     b.warp_w = t->launch.warp_w;
     b.order = t->launch.order;
     b.persistent = t->launch.persistent;
+    b.tw_log = (uint32_t)__builtin_ctz(t->launch.tile_w);
+    b.th_log = (uint32_t)__builtin_ctz(t->launch.tile_h);
+    b.ww_log = (uint32_t)__builtin_ctz(t->launch.warp_w);
     const bool bwd = grad != nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     if (n_views <= (uint32_t)lfk::kSmallViews) return run_chunk<lfk::kSmallViews>(t, b, views, n_views, bwd, st);

@@ -348,7 +348,7 @@ struct Top5 {
 };
 
 // Exact ranking in FP64 over the same candidates (rare: an uncertain order).
-__device__ __noinline__ Top5 knn5_fp64(const PointSetK P, const SphereK S, float3 h, const Source src,
+__device__ __forceinline__ Top5 knn5_fp64(const PointSetK P, const SphereK S, float3 h, const Source src,
                                        float3 qh, float3 ql)
 {
     double q[3];

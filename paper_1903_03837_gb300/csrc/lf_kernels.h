@@ -27,6 +27,7 @@ struct RenderParamsBase {
     uint32_t *status, *queue, *done;
     uint32_t n_views, total_tiles;
     uint32_t tile_w, tile_h, warp_w, order, persistent;
+    uint32_t tw_log, th_log, ww_log;   // log2 of tile_w, tile_h, warp_w
 };
 
 template <int MAXV>

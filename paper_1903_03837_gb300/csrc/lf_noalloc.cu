@@ -161,6 +161,7 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
         L = *launch;
         uint32_t ww = L.warp_w;
         bool ok = (ww == 1 || ww == 2 || ww == 4 || ww == 8 || ww == 16 || ww == 32) && L.tile_w && L.tile_h &&
+                  !(L.tile_w & (L.tile_w - 1)) && !(L.tile_h & (L.tile_h - 1)) &&
                   L.tile_w % ww == 0 && L.tile_h % (32 / ww) == 0 && L.tile_w * L.tile_h <= (uint32_t)lfk::kMaxBlock &&
                   L.order <= 1 && L.persistent <= 1 && L.ctas_per_sm <= 64;
         if (!ok) return na_fail(LF_ERR_INVALID_ARG, "inconsistent launch shape");
@@ -210,6 +211,9 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
     b.warp_w = L.warp_w;
     b.order = L.order;
     b.persistent = L.persistent;
+    b.tw_log = (uint32_t)__builtin_ctz(L.tile_w);
+    b.th_log = (uint32_t)__builtin_ctz(L.tile_h);
+    b.ww_log = (uint32_t)__builtin_ctz(L.warp_w);
     int kind = !quant ? (C == 4 ? lfk::kF32C4 : lfk::kF32C3) : (d->dtype == LF_DTYPE_F16 ? lfk::kF16C4 : lfk::kE4M3C4);
     if (n_views <= (uint32_t)lfk::kSmallViews)
         return launch_views<lfk::kSmallViews>(b, L, kind, sm_count, views, n_views, st);

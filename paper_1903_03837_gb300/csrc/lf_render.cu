@@ -20,6 +20,8 @@
 
 namespace lfk {
 
+// Tile t of the launch -> (view, tile column, tile row). Runs in one thread
+// per CTA; the result is shared through shared memory.
 __device__ __forceinline__ void tile_of(const RenderParamsBase &p, const ViewK *views,
                                         const uint32_t *prefix, uint32_t nv, uint32_t t,
                                         uint32_t &v, uint32_t &tx, uint32_t &ty)
@@ -33,25 +35,26 @@ __device__ __forceinline__ void tile_of(const RenderParamsBase &p, const ViewK *
     uint32_t lt = t - prefix[v];
     uint32_t tiles_x = views[v].tiles_x;
     if (p.order == 0) {
-        tx = lt % tiles_x;
         ty = lt / tiles_x;
+        tx = lt - ty * tiles_x;
     } else {                           // strips of kStripTiles tile rows, column by column
         uint32_t strip = lt / (tiles_x * kStripTiles);
         uint32_t r = lt - strip * tiles_x * kStripTiles;
         uint32_t hs = min(kStripTiles, views[v].tiles_y - strip * kStripTiles);
         tx = r / hs;
-        ty = strip * kStripTiles + r % hs;
+        ty = strip * kStripTiles + (r - tx * hs);
     }
 }
 
+// Pixel of this thread in tile (tx, ty): tile and warp shapes are powers of
+// two, so the mapping is shifts and masks.
 __device__ __forceinline__ void pixel_of(const RenderParamsBase &p, uint32_t tx, uint32_t ty,
                                          uint32_t &px, uint32_t &py)
 {
     uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t warp_h = 32u / p.warp_w;
-    uint32_t warps_x = p.tile_w / p.warp_w;
-    px = tx * p.tile_w + (warp % warps_x) * p.warp_w + lane % p.warp_w;
-    py = ty * p.tile_h + (warp / warps_x) * warp_h + lane / p.warp_w;
+    uint32_t wx_log = p.tw_log - p.ww_log;              // log2(warps per tile row)
+    px = (tx << p.tw_log) + ((warp & ((1u << wx_log) - 1u)) << p.ww_log) + (lane & ((1u << p.ww_log) - 1u));
+    py = (ty << p.th_log) + ((warp >> wx_log) << (5u - p.ww_log)) + (lane >> p.ww_log);
 }
 
 // Indices and normalised weights of one ray; false for a miss.
@@ -211,19 +214,23 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
 template <int DT, int MAXV, bool BWD>
 __global__ void __launch_bounds__(kMaxBlock, LF_MIN_BLOCKS) render_kernel(const __grid_constant__ RenderParams<MAXV> p)
 {
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_tile[4];     // view, tile column, tile row, valid
     const uint32_t nv = p.n_views;
-    uint32_t t = p.persistent ? 0u : blockIdx.x;
     for (;;) {
-        if (p.persistent) {
-            if (threadIdx.x == 0) s_tile = atomicAdd(p.queue, 1u);
-            __syncthreads();
-            t = s_tile;
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = p.persistent ? atomicAdd(p.queue, 1u) : blockIdx.x;
+            uint32_t v = 0, tx = 0, ty = 0;
+            bool ok = t < p.total_tiles;
+            if (ok) tile_of(p, p.views, p.tile_prefix, nv, t, v, tx, ty);
+            s_tile[0] = v;
+            s_tile[1] = tx;
+            s_tile[2] = ty;
+            s_tile[3] = ok;
         }
-        if (t >= p.total_tiles) break;
-        uint32_t v, tx, ty, px, py;
-        tile_of(p, p.views, p.tile_prefix, nv, t, v, tx, ty);
+        __syncthreads();
+        const uint32_t v = s_tile[0], tx = s_tile[1], ty = s_tile[2];
+        if (!s_tile[3]) break;
+        uint32_t px, py;
         pixel_of(p, tx, ty, px, py);
         const ViewK &vw = p.views[v];
         bool active = px < vw.width && py < vw.height;
@@ -233,6 +240,7 @@ __global__ void __launch_bounds__(kMaxBlock, LF_MIN_BLOCKS) render_kernel(const 
             if (active) render_ray<DT>(p, vw, px, py);
         }
         if (!p.persistent) break;
+        __syncthreads();               // everyone has read s_tile before it is rewritten
     }
     if (p.persistent && threadIdx.x == 0) {
         __threadfence();
