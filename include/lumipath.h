@@ -51,6 +51,12 @@ typedef enum lf_dtype {
 
 /* lf_table_desc.flags */
 #define LF_TABLE_BORROW 0x1u   /* keep the caller's device pointers instead of copying */
+/* Only the origin rows of the upper hemisphere are stored (Section 3: z_i > 0,
+ * i.e. i < M/2): the table has floor(M/2) rows (and scales). Origin neighbours
+ * outside the stored rows are dropped and the remaining origin weights
+ * renormalised; a ray whose 5 origin neighbours are all unstored is masked
+ * (written as a miss). */
+#define LF_TABLE_UPPER_HEMISPHERE 0x2u
 
 /* Description of a light-field table (Section 2: sphere S with radius R and
  * origin O; point counts M and N; the texture L^(i,j) of M x N texels). */
@@ -99,11 +105,11 @@ typedef struct lf_launch {
 typedef struct lf_table lf_table;
 
 /* Create a table on the current device.
- * radiance_dev: device array [M][N][C_s] in row-major order (origin row i,
- *   direction column j, channel c), where C_s = C for F32 and for C = 4, and
- *   C_s = C for the copied F16/E4M3 forms; element type per dtype (float,
- *   uint16 binary16 bits, uint8 E4M3 bits).
- * row_scales_dev: device array [M] of FP32 scales; required for F16/E4M3,
+ * radiance_dev: device array [M'][N][C] in row-major order (origin row i,
+ *   direction column j, channel c), M' = M, or floor(M/2) with
+ *   LF_TABLE_UPPER_HEMISPHERE; element type per dtype (float, uint16 binary16
+ *   bits, uint8 E4M3 bits).
+ * row_scales_dev: device array [M'] of FP32 scales; required for F16/E4M3,
  *   ignored (may be NULL) for F32.
  * Without LF_TABLE_BORROW the table and scales are copied (FP16/E4M3 texels
  *   padded to 4 channels) and the caller may free its arrays once the stream
@@ -132,7 +138,7 @@ lf_status lf_render(const lf_table *t, const lf_view *views_host, uint32_t n_vie
 /* Gradient of the render with respect to the table: for every hit ray and
  * every tap (a, b), grad_table[i_a][j_b][c] += W_ab * grad_out[ray][c]
  * (the adjoint of the linear blend). grad_out_dev: device FP32 [P][C];
- * grad_table_dev: device FP32 [M][N][C], accumulated (not cleared) with
+ * grad_table_dev: device FP32 [M'][N][C], accumulated (not cleared) with
  * warp-aggregated atomic adds, so the summation order is not fixed.
  * Errors: LF_ERR_INVALID_ARG, LF_ERR_CUDA. */
 lf_status lf_render_backward(const lf_table *t, const lf_view *views_host, uint32_t n_views,

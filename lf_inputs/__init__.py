@@ -224,12 +224,24 @@ def config_large(seed: int = 0, frame: int = 0) -> Config:
                   orbit_frame(frame), extra={"frames": 240, "frame": frame})
 
 
+def config_paper(seed: int = 0, width: int = 1280, height: int = 720) -> Config:
+    """The paper's own table shape: M = 12,288 origins of which only the upper
+    hemisphere (6,144 rows) is stored, N = 23,576 directions, 4-byte texels
+    (E4M3 RGBA): 0.5 x 12,288 x 23,576 x 4 B = 579,403,776 B. A stereo pair of
+    1280x720 views at 2.5R, 35 degrees above the equator, looking at the centre."""
+    el, az = math.radians(35.0), math.radians(30.0)
+    c = 2.5 * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+    views = pack_offsets(list(stereo_pair(c, (0.0, 0.0, 0.0), width, height, 1.0)))
+    return Config("paper", 12288, 23576, 4, 16, seed, ("e4m3",), views, extra={"upper": True})
+
+
 CONFIGS = {
     "small": config_small,
     "precision": config_precision,
     "batching": config_batching,
     "differentiation": config_differentiation,
     "large": config_large,
+    "paper": config_paper,
 }
 
 

@@ -65,7 +65,7 @@ class _Scene(C.Structure):
                 ("N", C.c_uint32), ("C", C.c_uint32), ("K", C.c_int),
                 ("Po", C.c_void_p), ("Pd", C.c_void_p), ("dtype", C.c_int),
                 ("table", C.c_void_p), ("scales", C.c_void_p), ("lobes", C.c_void_p),
-                ("rowmap", C.c_void_p)]
+                ("rowmap", C.c_void_p), ("upper", C.c_int)]
 
 
 def lib():
@@ -84,6 +84,7 @@ def lib():
                 "lfo_knn": (C.c_int, [vp, u32, vp, C.c_int, vp, vp]),
                 "lfo_kernel_sigma": (dbl, [u32]),
                 "lfo_tent_weights": (None, [vp, C.c_int, u32, vp]),
+                "lfo_tent_weights_kept": (None, [vp, vp, C.c_int, u32, C.c_int32, vp]),
                 "lfo_f16_decode": (dbl, [C.c_uint16]),
                 "lfo_f16_encode": (C.c_uint16, [C.c_float]),
                 "lfo_e4m3_decode": (dbl, [C.c_uint8]),
@@ -190,6 +191,14 @@ def kernel_sigma(n: int) -> float:
     return lib().lfo_kernel_sigma(n)
 
 
+def tent_weights_kept(d2, idx, n: int, rows: int) -> np.ndarray:
+    d2 = np.ascontiguousarray(d2, np.float64)
+    idx = np.ascontiguousarray(idx, np.int32)
+    w = np.zeros(len(d2))
+    lib().lfo_tent_weights_kept(_p(d2), _p(idx), len(d2), n, rows, _p(w))
+    return w
+
+
 def tent_weights(d2, n: int) -> np.ndarray:
     d2 = np.ascontiguousarray(d2, np.float64)
     w = np.zeros(len(d2))
@@ -293,17 +302,20 @@ class Scene:
     table kinds: ``f32`` (FP32 [M,N,C]), ``f16`` / ``e4m3`` (codes [M,N,C] and
     FP32 per-row scales), ``lobe`` (the lobe field evaluated in FP64 on demand).
     With ``rows`` (a list of origin rows), ``table``/``scales`` hold only those
-    rows, in that order; reading any other row yields NaN.
+    rows, in that order; reading any other row yields NaN. With ``upper``, only
+    the upper-hemisphere origin rows i < M/2 exist (the table has M/2 rows):
+    other origin neighbours are dropped and a pixel with none left is masked.
     """
 
     def __init__(self, M: int, N: int, Cc: int, kind: str = "f32", table=None, scales=None,
-                 lobes=None, R: float = 1.0, O=(0.0, 0.0, 0.0), K: int = 5, rows=None):
+                 lobes=None, R: float = 1.0, O=(0.0, 0.0, 0.0), K: int = 5, rows=None,
+                 upper: bool = False):
         self.M, self.N, self.C, self.K, self.kind = M, N, Cc, K, kind
         self.R, self.O = float(R), tuple(float(o) for o in O)
         self.Po, self.Pd = sf_points(M), sf_points(N)
         dt = {"f32": 0, "f16": 1, "e4m3": 2, "lobe": 3}[kind]
         tptr = sptr = lptr = rptr = None
-        nrows = M
+        nrows = M // 2 if upper else M
         if rows is not None:
             rows = np.asarray(rows, np.int64)
             nrows = len(rows)
@@ -322,7 +334,7 @@ class Scene:
             self._lh = _LobesHold(lobes)
             lptr = C.cast(C.pointer(self._lh.s), C.c_void_p).value
         self.s = _Scene(self.R, (C.c_double * 3)(*self.O), M, N, Cc, K, _p(self.Po).value,
-                        _p(self.Pd).value, dt, tptr, sptr, lptr, rptr)
+                        _p(self.Pd).value, dt, tptr, sptr, lptr, rptr, 1 if upper else 0)
 
 
 def _views_arrays(views):
@@ -373,7 +385,7 @@ def render_backward(scene: Scene, views, pix: np.ndarray, grad_out: np.ndarray) 
     pix = np.ascontiguousarray(pix, np.uint32)
     g = np.ascontiguousarray(grad_out, np.float64).reshape(pix.shape[0], scene.C)
     vf, wh = _views_arrays(views)
-    G = np.zeros((scene.M, scene.N, scene.C))
+    G = np.zeros((scene.M // 2 if scene.s.upper else scene.M, scene.N, scene.C))
     lib().lfo_render_backward_pixels(C.byref(scene.s), _p(vf), _p(wh), _p(pix), pix.shape[0],
                                      _p(g), _p(G))
     return G

@@ -158,6 +158,27 @@ void lfo_tent_weights(const double *d2, int cnt, uint32_t n, double *w)
     }
 }
 
+/* Tent weights over the neighbours with index < rows only (others weigh 0),  */
+/* normalised over those; if all of them are 0 the nearest kept one takes 1.   */
+void lfo_tent_weights_kept(const double *d2, const int32_t *idx, int cnt, uint32_t n, int32_t rows,
+                           double *w)
+{
+    double sigma = lfo_kernel_sigma(n), S = 0.0;
+    int first = -1;
+    for (int a = 0; a < cnt; ++a) {
+        int keep = idx[a] < rows;
+        if (keep && first < 0) first = a;
+        double v = keep ? 1.0 - sqrt(d2[a]) / sigma : 0.0;
+        w[a] = v > 0.0 ? v : 0.0;
+        S += w[a];
+    }
+    if (S > 0.0) {
+        for (int a = 0; a < cnt; ++a) w[a] /= S;
+    } else {
+        for (int a = 0; a < cnt; ++a) w[a] = (a == first) ? 1.0 : 0.0;
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Quantisers.                                                                */
 /* IEEE 754 binary16: 1 sign, 5 exponent (bias 15), 10 fraction bits.         */
@@ -323,6 +344,7 @@ typedef struct {
     const float *scales;     /* [M] for dtype 1, 2 */
     const lfo_lobes *lobes;  /* dtype 3 */
     const int32_t *rowmap;   /* optional [M]: table/scale row holding origin row i (-1: absent) */
+    int upper;               /* 1: only the upper-hemisphere origin rows (z_i > 0, i < M/2) exist */
 } lfo_scene;
 
 static void lfo_fetch(const lfo_scene *S, uint32_t i, uint32_t j, double *v)
@@ -365,7 +387,17 @@ static int lfo_pixel_samples(const lfo_scene *S, const float *vw, uint32_t W, ui
     lfo_normalize_hit(hd, S->O, qd);
     *ko = lfo_knn(S->Po, S->M, qo, S->K, io, d2o);
     *kd = lfo_knn(S->Pd, S->N, qd, S->K, jd, d2d);
-    lfo_tent_weights(d2o, *ko, S->M, wo);
+    if (S->upper) {
+        /* Section 3: only origins of the upper hemisphere are stored. Origin
+         * neighbours outside the stored rows are dropped and the remaining
+         * weights renormalised; a pixel with none left is masked (as a miss). */
+        int kept = 0;
+        for (int a = 0; a < *ko; ++a) kept += io[a] < (int32_t)(S->M / 2);
+        if (!kept) return 0;
+        lfo_tent_weights_kept(d2o, io, *ko, S->M, (int32_t)(S->M / 2), wo);
+    } else {
+        lfo_tent_weights(d2o, *ko, S->M, wo);
+    }
     lfo_tent_weights(d2d, *kd, S->N, wd);
     return 1;
 }
@@ -390,6 +422,7 @@ int64_t lfo_render_pixels(const lfo_scene *S, const float *views, const uint32_t
         ++hits;
         for (int a = 0; a < ko; ++a)
             for (int b = 0; b < kd; ++b) {
+                if (S->upper && io[a] >= (int32_t)(S->M / 2)) continue;   /* not stored */
                 double W = wo[a] * wd[b];
                 lfo_fetch(S, (uint32_t)io[a], (uint32_t)jd[b], t);
                 for (uint32_t c = 0; c < S->C; ++c) out[p * S->C + c] += W * t[c];
@@ -416,6 +449,7 @@ void lfo_render_backward_pixels(const lfo_scene *S, const float *views, const ui
             continue;
         for (int a = 0; a < ko; ++a)
             for (int b = 0; b < kd; ++b) {
+                if (S->upper && io[a] >= (int32_t)(S->M / 2)) continue;   /* not stored */
                 double W = wo[a] * wd[b];
                 size_t base = ((size_t)io[a] * S->N + (size_t)jd[b]) * S->C;
                 for (uint32_t c = 0; c < S->C; ++c) G[base + c] += W * g[p * S->C + c];

@@ -178,6 +178,8 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
     b.tw_log = (uint32_t)__builtin_ctz(t->launch.tile_w);
     b.th_log = (uint32_t)__builtin_ctz(t->launch.tile_h);
     b.ww_log = (uint32_t)__builtin_ctz(t->launch.warp_w);
+    b.rows_valid = t->rows;
+    b.rows_stored = (t->desc.flags & LF_TABLE_UPPER_HEMISPHERE) ? t->rows : 0u;
     const bool bwd = grad != nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     if (n_views <= (uint32_t)lfk::kSmallViews) return run_chunk<lfk::kSmallViews>(t, b, views, n_views, bwd, st);
@@ -195,6 +197,17 @@ size_t code_bytes(int dtype) { return dtype == LF_DTYPE_F32 ? 4 : (dtype == LF_D
 
 namespace lfk {
 void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
+void fill_sphere_consts(SphereK &S, double R, const double O[3])
+{
+    double ir = 1.0 / R, r2 = R * R;
+    S.ir_h = (float)ir;
+    S.ir_l = (float)(ir - (double)S.ir_h);
+    S.r2_h = (float)r2;
+    S.r2_l = (float)(r2 - (double)S.r2_h);
+    S.inv_r2 = (float)(1.0 / r2);
+    S.centred = (O[0] == 0.0 && O[1] == 0.0 && O[2] == 0.0) ? 1u : 0u;
+}
 }  // namespace lfk
 
 extern "C" {
@@ -241,13 +254,17 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
         return fail(LF_ERR_INVALID_ARG, "unknown dtype %d", d->dtype);
     if (d->k_nearest != 0 && d->k_nearest != 5)
         return fail(LF_ERR_UNSUPPORTED, "k_nearest=%u: only 5 neighbours per hit are built", d->k_nearest);
-    if (d->flags & ~LF_TABLE_BORROW) return fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
+    if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
+        return fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
+    const bool upper = (d->flags & LF_TABLE_UPPER_HEMISPHERE) != 0;
+    if (upper && M < 2) return fail(LF_ERR_INVALID_ARG, "an upper-hemisphere table needs M >= 2");
+    const uint32_t rows = upper ? M / 2 : M;
     const bool quant = d->dtype != LF_DTYPE_F32;
     if (quant && !row_scales_dev) return fail(LF_ERR_INVALID_ARG, "F16/E4M3 tables need row scales");
     const bool borrow = (d->flags & LF_TABLE_BORROW) != 0;
     if (borrow && quant && C != 4)
         return fail(LF_ERR_INVALID_ARG, "a borrowed F16/E4M3 table must have 4 channels");
-    const uint64_t texels = (uint64_t)M * N;
+    const uint64_t texels = (uint64_t)rows * N;
     if (texels > (1ull << 40)) return fail(LF_ERR_INVALID_ARG, "table too large");
 
     lf_table *t = new (std::nothrow) lf_table;
@@ -255,6 +272,7 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
     memset(t, 0, sizeof *t);
     t->desc = *d;
     t->C = C;
+    t->rows = rows;
     t->launch = default_launch();
     cudaGetDevice(&t->device);
     t->sm_count = lf_device_sm_count();
@@ -284,21 +302,22 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
         e = cudaMalloc(&t->owned_texels, texels * Cs * cb);
         if (e != cudaSuccess) return bail(cuda_fail(e, "table allocation"));
         if (quant && C == 3)
-            e = lfk::launch_pad_codes(radiance_dev, M, N, (int)cb, t->owned_texels, st);
+            e = lfk::launch_pad_codes(radiance_dev, rows, N, (int)cb, t->owned_texels, st);
         else
             e = cudaMemcpyAsync(t->owned_texels, radiance_dev, texels * Cs * cb, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return bail(cuda_fail(e, "table copy"));
         t->texels = t->owned_texels;
         if (quant) {
-            e = cudaMalloc(&t->owned_scales, sizeof(float) * M);
+            e = cudaMalloc(&t->owned_scales, sizeof(float) * rows);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(t->owned_scales, row_scales_dev, sizeof(float) * M, cudaMemcpyDeviceToDevice, st);
+                e = cudaMemcpyAsync(t->owned_scales, row_scales_dev, sizeof(float) * rows, cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) return bail(cuda_fail(e, "scale copy"));
             t->scales = t->owned_scales;
         }
     }
 
     lfk::SphereK &S = t->sphere;
+    lfk::fill_sphere_consts(S, d->radius, d->center);
     S.r32 = (float)d->radius;
     for (int k = 0; k < 3; ++k) {
         S.o32[k] = (float)d->center[k];

@@ -46,6 +46,30 @@ constexpr float kInvLog2Phi2 = 0.72021234840458929f;    // 1 / log2(Phi^2)
 constexpr float kSqrt5Pi = 7.0248147310407731f;          // sqrt(5)*pi
 constexpr float kInv2Pi = 0.15915494309189535f;
 
+// Azimuth of (x, y) in turns, for choosing the lattice cell only. atan on
+// [0, 1] is a degree-15 odd polynomial whose coefficients were fitted for this
+// library by weighted least squares on Chebyshev nodes (max error 8.8e-8 rad);
+// any value congruent modulo whole turns gives the same cell, and the window
+// tolerates an error of 2e-3 cells.
+__device__ __forceinline__ float azimuth_turns(float y, float x)
+{
+    constexpr float kAtanC[8] = {0.9999999544831605f, -0.3333228719074749f, 0.19973502132375778f,
+                                 -0.14039253597339113f, 0.09965704508344218f, -0.06018953709746647f,
+                                 0.024736771941069477f, -0.004825772341815579f};
+    float ax = fabsf(x), ay = fabsf(y);
+    float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    float a = __fdividef(mn, fmaxf(mx, 1e-30f));
+    float a2 = a * a;
+    float p = kAtanC[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) p = __fmaf_rn(p, a2, kAtanC[k]);
+    float r = a * p;                                   // atan(mn/mx) in [0, pi/4]
+    r = ay > ax ? 1.57079632679f - r : r;
+    r = x < 0.0f ? 3.14159265359f - r : r;
+    r = y < 0.0f ? -r : r;
+    return r * kInv2Pi;
+}
+
 // ---------------------------------------------------------------------------
 // Camera ray and sphere intersection: IEEE FP32, fixed order, no contraction.
 // ---------------------------------------------------------------------------
@@ -117,16 +141,10 @@ __device__ __forceinline__ df df_mul(df x, df y)
     return fast_two_sum(p, e);
 }
 
-// Unit vector (h - O)/|h - O| as hi/lo float3 pairs; |error| about 2^-44.
-__device__ __forceinline__ void unit_hit_df(const SphereK &S, float3 h, float3 &qh, float3 &ql)
+// Unit vector (h - O)/|h - O| as hi/lo float3 pairs by a double-float Newton
+// step from rsqrt (|error| about 2^-44); used when h lies far off the sphere.
+__device__ __forceinline__ void unit_hit_df_newton(df f[3], float3 &qh, float3 &ql)
 {
-    df f[3];
-    const float hv[3] = {h.x, h.y, h.z};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        df s = two_sum(hv[k], -S.o_hi[k]);
-        f[k] = fast_two_sum(s.h, __fsub_rn(s.l, S.o_lo[k]));
-    }
     df r2 = df_add(df_add(df_mul(f[0], f[0]), df_mul(f[1], f[1])), df_mul(f[2], f[2]));
     float y0 = rsqrtf(r2.h);
     df t = df_mul(r2, df{__fmul_rn(y0, y0), __fmaf_rn(y0, y0, -__fmul_rn(y0, y0))});
@@ -135,6 +153,59 @@ __device__ __forceinline__ void unit_hit_df(const SphereK &S, float3 h, float3 &
     df q0 = df_mul(f[0], y), q1 = df_mul(f[1], y), q2 = df_mul(f[2], y);
     qh = make_float3(q0.h, q1.h, q2.h);
     ql = make_float3(q0.l, q1.l, q2.l);
+}
+
+// Unit vector (h - O)/|h - O| as hi/lo float3 pairs. The hit h lies on S up to
+// FP32 rounding, so |h - O|^2 = R^2 (1 + eps) with tiny eps, and
+// 1/|h - O| = (1/R)(1 - eps/2 + 3 eps^2/8 - 5 eps^3/16 + ...). eps is formed
+// from an error-free expansion of |h - O|^2 - R^2; for |eps| <= 2^-12 the
+// result is within about 2^-37 of the exact unit vector (2^-45 for the
+// |eps| ~ 1e-6 of cameras a few radii away), otherwise the Newton form runs.
+__device__ __forceinline__ void unit_hit_df(const SphereK &S, float3 h, float3 &qh, float3 &ql)
+{
+    df f[3];
+    const float hv[3] = {h.x, h.y, h.z};
+    if (S.centred) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) f[k] = df{hv[k], 0.0f};
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            df s = two_sum(hv[k], -S.o_hi[k]);
+            f[k] = fast_two_sum(s.h, __fsub_rn(s.l, S.o_lo[k]));
+        }
+    }
+    // |f|^2 - R^2 = sum_k (fh^2 + err(fh^2) + 2 fh fl) - (r2_h + r2_l), cancellation-free
+    float p0 = __fmul_rn(f[0].h, f[0].h), p1 = __fmul_rn(f[1].h, f[1].h), p2 = __fmul_rn(f[2].h, f[2].h);
+    float small = __fmaf_rn(f[0].h, f[0].h, -p0);
+    small = __fadd_rn(small, __fmaf_rn(f[1].h, f[1].h, -p1));
+    small = __fadd_rn(small, __fmaf_rn(f[2].h, f[2].h, -p2));
+    small = __fmaf_rn(2.0f * f[0].h, f[0].l, small);
+    small = __fmaf_rn(2.0f * f[1].h, f[1].l, small);
+    small = __fmaf_rn(2.0f * f[2].h, f[2].l, small);
+    df a = two_sum(p0, p1);
+    df b = two_sum(a.h, p2);
+    df c = two_sum(b.h, -S.r2_h);
+    float d = __fadd_rn(__fadd_rn(__fadd_rn(c.h, c.l), __fadd_rn(a.l, b.l)), __fsub_rn(small, S.r2_l));
+    float eps = __fmul_rn(d, S.inv_r2);
+    if (!(fabsf(eps) <= 0x1p-12f)) {
+        unit_hit_df_newton(f, qh, ql);
+        return;
+    }
+    float delta = eps * __fmaf_rn(eps, __fmaf_rn(-0.3125f, eps, 0.375f), -0.5f);
+    const float s_h = S.ir_h, s_l = __fmaf_rn(S.ir_h, delta, S.ir_l);
+    float qhv[3], qlv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float pr = __fmul_rn(f[k].h, s_h);
+        float er = __fmaf_rn(f[k].h, s_h, -pr);
+        er = __fmaf_rn(f[k].h, s_l, __fmaf_rn(f[k].l, s_h, er));
+        df q = fast_two_sum(pr, er);
+        qhv[k] = q.h;
+        qlv[k] = q.l;
+    }
+    qh = make_float3(qhv[0], qhv[1], qhv[2]);
+    ql = make_float3(qlv[0], qlv[1], qlv[2]);
 }
 
 // FP64 unit hit vector in the operation order of the FP64 definition.
@@ -244,7 +315,7 @@ __device__ __forceinline__ Window lattice_window(const PointSetK &P, float3 qh)
 {
     float z = qh.z;
     float omz2 = __fmul_rn(__fsub_rn(1.0f, z), __fadd_rn(1.0f, z));
-    float t = atan2f(qh.y, qh.x) * kInv2Pi;                        // turns
+    float t = azimuth_turns(qh.y, qh.x);                            // turns
     float ic = (P.nf * (1.0f - z) - 1.0f) * 0.5f;                  // continuous index
     int k = __float2int_rd(__log2f(kSqrt5Pi * P.nf * omz2) * kInvLog2Phi2);
     k = max(2, min(k, kFibN - 3));
@@ -498,6 +569,35 @@ __device__ __forceinline__ void tent_weights(const float d2[5], int cnt, float i
 #pragma unroll
         for (int m = 0; m < 5; ++m) w[m] = (m == 0) ? 1.0f : 0.0f;
     }
+}
+
+// Tent weights over the neighbours with index < rows only (the stored origin
+// rows of an upper-hemisphere table), normalised over those; if all of them
+// are 0 the nearest kept neighbour takes weight 1. Returns false when no
+// neighbour is kept (the ray is masked).
+__device__ __forceinline__ bool tent_weights_kept(const float d2[5], const int32_t idx[5], int cnt,
+                                                  float inv_sigma, uint32_t rows, float w[5])
+{
+    float S = 0.0f;
+    int first = -1;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        bool keep = m < cnt && (uint32_t)idx[m] < rows;
+        first = (keep && first < 0) ? m : first;
+        float d = d2[m] * rsqrtf(fmaxf(d2[m], 1e-37f));
+        w[m] = keep ? fmaxf(0.0f, 1.0f - d * inv_sigma) : 0.0f;
+        S += w[m];
+    }
+    if (first < 0) return false;
+    if (S > 0.0f) {
+        float r = __frcp_rn(S);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) w[m] *= r;
+    } else {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) w[m] = (m == first) ? 1.0f : 0.0f;
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------------------

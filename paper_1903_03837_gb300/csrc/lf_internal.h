@@ -27,6 +27,10 @@ struct SphereK {
     float r32;
     float o_hi[3], o_lo[3];
     double o64[3];
+    float ir_h, ir_l;        // 1/R as a hi/lo pair
+    float r2_h, r2_l;        // R^2 as a hi/lo pair
+    float inv_r2;            // 1/R^2
+    uint32_t centred;        // O == (0, 0, 0)
 };
 
 // One SF point set: p_i as hi/lo float4 pairs (w unused), n, n as float and
@@ -46,6 +50,7 @@ struct lf_table {
     int device;
     int texel_kind;                  // lfk::TexelKind
     uint32_t C;                      // logical channels (3 or 4)
+    uint32_t rows;                   // origin rows stored (M, or M/2 for the upper hemisphere)
     const void *texels;              // [M][N][Cs]
     const float *scales;             // [M] or NULL (F32)
     void *owned_texels;              // non-NULL if the library owns the copy

@@ -28,6 +28,8 @@ struct RenderParamsBase {
     uint32_t n_views, total_tiles;
     uint32_t tile_w, tile_h, warp_w, order, persistent;
     uint32_t tw_log, th_log, ww_log;   // log2 of tile_w, tile_h, warp_w
+    uint32_t rows_stored;              // origin rows present (upper hemisphere), 0: all
+    uint32_t rows_valid;               // rows of the table (M or rows_stored)
 };
 
 template <int MAXV>
@@ -57,6 +59,10 @@ struct LobeParams {
 cudaError_t launch_fill_lobe(const LobeParams &P, const float4 *po_hi, const float4 *po_lo,
                              const float4 *pd_hi, const float4 *pd_lo, uint32_t M, uint32_t N,
                              float *out, cudaStream_t st);
+
+// Host-side constants of the sphere used by the unit-hit step: 1/R and R^2 as
+// hi/lo float pairs, 1/R^2, and whether O is the origin (lf_abi.cu).
+void fill_sphere_consts(SphereK &S, double R, const double O[3]);
 
 // Sets the calling thread's lf_last_error() message (lf_abi.cu).
 void set_last_error(const char *msg);

@@ -143,6 +143,10 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
         return na_fail(LF_ERR_INVALID_ARG, "F16/E4M3 tables need 4 channels and row scales here");
     if (d->k_nearest != 0 && d->k_nearest != 5)
         return na_fail(LF_ERR_UNSUPPORTED, "only 5 neighbours per hit are built");
+    if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
+        return na_fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
+    if ((d->flags & LF_TABLE_UPPER_HEMISPHERE) && M < 2)
+        return na_fail(LF_ERR_INVALID_ARG, "an upper-hemisphere table needs M >= 2");
     if (n_views == 0 || n_views > 65536) return na_fail(LF_ERR_INVALID_ARG, "n_views must be in [1, 65536]");
     for (uint32_t v = 0; v < n_views; ++v) {
         const lf_view &w = views[v];
@@ -187,6 +191,7 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
 
     lfk::RenderParamsBase b;
     memset(&b, 0, sizeof b);
+    lfk::fill_sphere_consts(b.sphere, d->radius, d->center);
     b.sphere.r32 = (float)d->radius;
     for (int k = 0; k < 3; ++k) {
         b.sphere.o32[k] = (float)d->center[k];
@@ -214,6 +219,9 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
     b.tw_log = (uint32_t)__builtin_ctz(L.tile_w);
     b.th_log = (uint32_t)__builtin_ctz(L.tile_h);
     b.ww_log = (uint32_t)__builtin_ctz(L.warp_w);
+    const bool upper = (d->flags & LF_TABLE_UPPER_HEMISPHERE) != 0;
+    b.rows_valid = upper ? M / 2 : M;
+    b.rows_stored = upper ? M / 2 : 0u;
     int kind = !quant ? (C == 4 ? lfk::kF32C4 : lfk::kF32C3) : (d->dtype == LF_DTYPE_F16 ? lfk::kF16C4 : lfk::kE4M3C4);
     if (n_views <= (uint32_t)lfk::kSmallViews)
         return launch_views<lfk::kSmallViews>(b, L, kind, sm_count, views, n_views, st);

@@ -76,7 +76,11 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
         P.inv_sigma = s ? p.pd.inv_sigma : p.po.inv_sigma;
         Top5 r = knn5(P, p.sphere, s ? hd : ho, p.status);
         float w[5];
-        tent_weights(r.d2, r.cnt, P.inv_sigma, w);
+        if (s == 0 && p.rows_stored) {
+            if (!tent_weights_kept(r.d2, r.i, r.cnt, P.inv_sigma, p.rows_stored, w)) return false;
+        } else {
+            tent_weights(r.d2, r.cnt, P.inv_sigma, w);
+        }
         if (s == 0) {
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
@@ -105,7 +109,8 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
     if (hit) {
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
-            int32_t i = max(io[a], 0);                 // a missing neighbour has weight 0
+            // a missing or unstored neighbour has weight 0 and reads row 0
+            int32_t i = (uint32_t)io[a] < p.rows_valid ? io[a] : 0;
             float s = wo[a];
             if constexpr (DT == kF16C4 || DT == kE4M3C4) s *= __ldg(p.scales + i);
             size_t row = (size_t)i * p.N;
@@ -190,7 +195,7 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
     for (int a = 0; a < 5; ++a) {
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
-            bool live = hit && io[a] >= 0 && jd[b] >= 0;
+            bool live = hit && (uint32_t)io[a] < p.rows_valid && jd[b] >= 0;
             uint64_t key = live ? (uint64_t)io[a] * p.N + (uint64_t)jd[b] : ~0ull - lane;
             float W = live ? wo[a] * wd[b] : 0.f;
             float4 val = make_float4(W * g.x, W * g.y, W * g.z, W * g.w);

@@ -19,6 +19,7 @@ LF_OK, LF_ERR_INVALID_ARG, LF_ERR_OUT_OF_MEMORY, LF_ERR_CUDA = 0, 1, 2, 3
 LF_ERR_UNSUPPORTED, LF_ERR_TIMEOUT, LF_ERR_DEVICE_CHECK = 4, 5, 6
 LF_DTYPE_F32, LF_DTYPE_F16, LF_DTYPE_E4M3 = 0, 1, 2
 LF_TABLE_BORROW = 0x1
+LF_TABLE_UPPER_HEMISPHERE = 0x2
 DTYPES = {"f32": LF_DTYPE_F32, "f16": LF_DTYPE_F16, "e4m3": LF_DTYPE_E4M3}
 
 

@@ -40,11 +40,15 @@ class LightField:
     """
 
     def __init__(self, radiance: torch.Tensor, dtype: str = "f32", scales: Optional[torch.Tensor] = None,
-                 R: float = 1.0, O=(0.0, 0.0, 0.0), borrow: bool = False):
+                 R: float = 1.0, O=(0.0, 0.0, 0.0), borrow: bool = False, n_origins: Optional[int] = None,
+                 upper: bool = False):
         _need_cuda(radiance, "radiance")
         if radiance.dim() != 3:
             raise ValueError("radiance must be [M, N, C]")
-        M, N, Cc = (int(s) for s in radiance.shape)
+        rows, N, Cc = (int(s) for s in radiance.shape)
+        M = int(n_origins) if n_origins is not None else (2 * rows if upper else rows)
+        if (M // 2 if upper else M) != rows:
+            raise ValueError(f"radiance has {rows} rows; expected {M // 2 if upper else M} for M={M}")
         ok = {"f32": (torch.float32,), "f16": (torch.int16, torch.float16),
               "e4m3": (torch.uint8, torch.int8, torch.float8_e4m3fn)}[dtype]
         if radiance.dtype not in ok:
@@ -56,9 +60,10 @@ class LightField:
         desc.center[:] = [float(o) for o in O]
         desc.n_origins, desc.n_directions, desc.channels = M, N, Cc
         desc.dtype = lp.DTYPES[dtype]
-        desc.flags = lp.LF_TABLE_BORROW if borrow else 0
+        desc.flags = (lp.LF_TABLE_BORROW if borrow else 0) | (lp.LF_TABLE_UPPER_HEMISPHERE if upper else 0)
         desc.k_nearest = 5
         self.M, self.N, self.C, self.dtype, self.R, self.O = M, N, Cc, dtype, float(R), tuple(O)
+        self.rows, self.upper = rows, bool(upper)
         self._keep = (radiance, scales) if borrow else None
         self.handle = lp.lf_create_table(desc, radiance.data_ptr(),
                                          scales.data_ptr() if scales is not None else None, _stream())
@@ -97,10 +102,10 @@ class LightField:
         if grad_out.dtype != torch.float32 or grad_out.numel() < total_pixels(views) * self.C:
             raise ValueError("grad_out must be float32 [P, C]")
         if grad_table is None:
-            grad_table = torch.zeros((self.M, self.N, self.C), dtype=torch.float32, device="cuda")
+            grad_table = torch.zeros((self.rows, self.N, self.C), dtype=torch.float32, device="cuda")
         _need_cuda(grad_table, "grad_table")
-        if grad_table.dtype != torch.float32 or grad_table.numel() != self.M * self.N * self.C:
-            raise ValueError("grad_table must be float32 [M, N, C]")
+        if grad_table.dtype != torch.float32 or grad_table.numel() != self.rows * self.N * self.C:
+            raise ValueError("grad_table must be float32 [rows, N, C]")
         vv = lp.make_views(views)
         lp.lf_render_backward(self.handle, vv, len(views), grad_out.data_ptr(), grad_table.data_ptr(), _stream())
         return grad_table

@@ -193,3 +193,30 @@ def test_differentiation_config_fit(api):
     assert p_fit > p_zero, (p_fit, p_zero)
     lf.close()
     lf_gt.close()
+
+
+def test_paper_shape_upper_hemisphere(api):
+    """The paper's table: M = 12,288 origins (upper 6,144 rows stored), N = 23,576,
+    4-byte E4M3 texels (579,403,776 bytes); a 1280x720 stereo pair."""
+    cfg = lf_inputs.config_paper()
+    lobes = cfg.lobes()
+    views = cfg.views
+    rows_stored = cfg.M // 2
+    T32 = api.fill_lobe_table(lobes, cfg.M, cfg.N)[:rows_stored].contiguous()
+    codes, s = api.quantize_table(T32, "e4m3")
+    assert codes.numel() == 579403776
+    lf = api.LightField(codes, "e4m3", s, borrow=True, n_origins=cfg.M, upper=True)
+    out, idx = lf.render(views, with_idx=True)
+    lf.sync_status()
+    pix = lf_inputs.sample_pixels(views, 2000, seed=5)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    _, want_idx, _ = oracle.render_pixels(oracle.Scene(cfg.M, cfg.N, 4, "lobe", lobes=lobes, upper=True),
+                                          views, pix)
+    rows = np.unique(want_idx[:, :5][(want_idx[:, :5] >= 0) & (want_idx[:, :5] < rows_stored)])
+    T_rows = oracle.lobe_table(lobes, cfg.M, cfg.N, rows=rows)
+    oc, os_ = oracle.quantize_rows(T_rows, "e4m3")
+    want_out, want_idx2, hits = oracle.render_pixels(
+        oracle.Scene(cfg.M, cfg.N, 4, "e4m3", oc, os_, rows=rows, upper=True), views, pix)
+    assert np.array_equal(want_idx, want_idx2) and hits > 200
+    check("paper/e4m3", out.cpu().numpy()[offs], idx.cpu().numpy()[offs], want_out, want_idx)
+    lf.close()

@@ -341,3 +341,34 @@ def test_index_step_stress_against_kdtree(api, M, N):
         bad = np.any(np.sort(idx[sub][:, cols], axis=1) != np.sort(nn, axis=1), axis=1)
         assert bad.sum() == 0, f"{bad.sum()} of {len(sub)} index sets differ from the k-d tree"
     assert len(sub) > 100000
+
+
+@pytest.mark.parametrize("dtype", ["f32", "e4m3"])
+def test_upper_hemisphere_table(api, dtype):
+    M, N = 3001, 700
+    rng = np.random.default_rng(31)
+    T = rng.uniform(0, 1, (M // 2, N, 4)).astype(np.float32)
+    views = lf_inputs.pack_offsets([lf_inputs.look_at((2.4, 0.3, 0.4), (0, 0, 0), 96, 80),
+                                    lf_inputs.look_at((0.2, 0.1, 2.6), (0, 0, 0), 40, 40),
+                                    lf_inputs.look_at((0.3, -0.2, -2.2), (0, 0, 0), 32, 32)])
+    if dtype == "f32":
+        sc = oracle.Scene(M, N, 4, "f32", T, upper=True)
+        tab, scales = torch.from_numpy(T).cuda(), None
+    else:
+        codes, s = oracle.quantize_rows(T, "e4m3")
+        sc = oracle.Scene(M, N, 4, "e4m3", codes, s, upper=True)
+        tab, scales = torch.from_numpy(codes).cuda(), torch.from_numpy(s).cuda()
+    want_out, want_idx, hits = oracle.render_views(sc, views)
+    lf = api.LightField(tab, dtype, scales, n_origins=M, upper=True)
+    out, idx = lf.render(views, with_idx=True)
+    lf.sync_status()
+    check_parity((out.cpu().numpy(), idx.cpu().numpy()), (want_out, want_idx))
+    # backward drops the unstored rows too
+    g = torch.from_numpy(rng.standard_normal(out.shape).astype(np.float32)).cuda()
+    G = lf.render_backward(views, g).cpu().numpy().astype(np.float64)
+    pix = lf_inputs.pixel_list(views)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    Gw = oracle.render_backward(oracle.Scene(M, N, 4, "f32", T, upper=True), views, pix,
+                                g.cpu().numpy()[offs].astype(np.float64))
+    assert np.abs(G - Gw).max() <= 2e-5 * max(1.0, np.abs(Gw).max())
+    lf.close()

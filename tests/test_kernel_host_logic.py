@@ -55,3 +55,33 @@ def test_lattice_offsets_follow_binet():
         # the basis (eps_k, F_k), (eps_{k+1}, F_{k+1}) has determinant
         # eps_k F_{k+1} - eps_{k+1} F_k = F_k^2 - F_{k-1} F_{k+1} = (-1)^(k+1) (Cassini): unimodular
         assert F[k] * F[k] - F[k - 1] * F[k + 1] == (-1) ** (k + 1)
+
+
+def test_azimuth_polynomial_accuracy():
+    """The kernel's atan polynomial, evaluated in float32 as the kernel does,
+    stays within 1e-6 rad of atan2 (the lattice window tolerates 2e-3 cells, i.e. about
+    1.9e-6 rad for the largest Fibonacci step of n = 2^24 points)."""
+    import numpy as np
+    src = open(DEV).read()
+    body = src[src.index("kAtanC[8] = {") + len("kAtanC[8] = {"):]
+    body = body[:body.index("}")]
+    c = [np.float32(float(v.strip().rstrip("f"))) for v in body.split(",")]
+    assert len(c) == 8
+    rng = np.random.default_rng(0)
+    ang = rng.uniform(-np.pi, np.pi, 200000)
+    rad = rng.uniform(1e-3, 1.0, 200000)
+    x = (rad * np.cos(ang)).astype(np.float32)
+    y = (rad * np.sin(ang)).astype(np.float32)
+    ax, ay = np.abs(x), np.abs(y)
+    a = (np.minimum(ax, ay) / np.maximum(ax, ay)).astype(np.float32)
+    a2 = (a * a).astype(np.float32)
+    p = np.full_like(a, c[7])
+    for k in range(6, -1, -1):
+        p = (p * a2 + c[k]).astype(np.float32)
+    r = (a * p).astype(np.float32)
+    r = np.where(ay > ax, np.float32(1.57079632679) - r, r)
+    r = np.where(x < 0, np.float32(3.14159265359) - r, r)
+    r = np.where(y < 0, -r, r)
+    ref = np.arctan2(y.astype(np.float64), x.astype(np.float64))
+    d = np.abs(np.angle(np.exp(1j * (r.astype(np.float64) - ref))))
+    assert d.max() < 1e-6

@@ -392,3 +392,50 @@ def test_psnr_definition():
     hit = np.array([True, True, False])
     assert oracle.psnr(ref, ref, hit) == float("inf")
     assert abs(oracle.psnr(ref, ref + 0.01, hit) - 10 * math.log10(1.0 / 1e-4)) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Upper-hemisphere storage (Section 3: only origins with z > 0 are stored)
+# --------------------------------------------------------------------------
+def test_upper_hemisphere_mode():
+    M, N = 400, 90
+    rng = np.random.default_rng(12)
+    T = rng.uniform(0, 1, (M, N, 3)).astype(np.float32)
+    top = lf_inputs.look_at((0.05, 0.1, 2.5), (0, 0, 0), 40, 40)
+    bottom = lf_inputs.look_at((0.05, 0.1, -2.5), (0, 0, 0), 40, 40)
+    full = oracle.Scene(M, N, 3, "f32", T)
+    up = oracle.Scene(M, N, 3, "f32", T[:M // 2], upper=True)
+    # seen from far above, every origin neighbour is stored: same image as the full table
+    a, ia, ha = oracle.render_views(full, [top])
+    b, ib, hb = oracle.render_views(up, [top])
+    assert ha == hb > 500
+    np.testing.assert_array_equal(ia, ib)
+    np.testing.assert_allclose(a, b, atol=1e-12)
+    # seen from below, every pixel is masked
+    c, ic, hc = oracle.render_views(up, [bottom])
+    assert hc == 0 and np.all(c == 0) and np.all(ic == -1)
+    # an oblique view: a pixel is masked exactly when all 5 origin neighbours lie in the
+    # lower half; a constant table renders its constant on every unmasked pixel
+    side = lf_inputs.look_at((2.4, 0.3, 0.4), (0, 0, 0), 48, 48)
+    K = np.full((M // 2, N, 3), 0.75, np.float32)
+    o, io, h = oracle.render_views(oracle.Scene(M, N, 3, "f32", K, upper=True), [side])
+    Po = oracle.sf_points(M)
+    masked = partial = 0
+    for p in lf_inputs.pixel_list([side])[::3]:
+        hit, _, _, _, qo, _ = oracle.trace_pixel(1.0, (0, 0, 0), side, p[1], p[2])
+        off = p[2] * 48 + p[1]
+        if not hit:
+            continue
+        nn, _ = oracle.knn(Po, qo, 5)
+        kept = nn < M // 2
+        if not kept.any():
+            masked += 1
+            assert io[off, 0] == -1 and np.all(o[off] == 0)
+        else:
+            partial += int(not kept.all())
+            assert list(io[off, :5]) == list(nn)
+            np.testing.assert_allclose(o[off], 0.75, rtol=1e-12)
+    assert masked > 10 and partial > 5
+    w = oracle.tent_weights_kept(np.array([0.0, 0.01, 0.02, 0.03, 0.04]) ** 2,
+                                 np.array([300, 10, 250, 20, 30]), M, M // 2)
+    assert w[0] == 0 and w[2] == 0 and abs(w.sum() - 1) < 1e-15
