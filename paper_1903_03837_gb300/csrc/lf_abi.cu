@@ -91,7 +91,7 @@ lf_status check_views(const lf_view *views, uint32_t n)
     return LF_OK;
 }
 
-lfk::ViewK to_viewk(const lf_view &w, const lf_launch &L)
+lfk::ViewK to_viewk(const lf_view &w, const lf_launch &L, const lf_table *t)
 {
     lfk::ViewK k;
     for (int i = 0; i < 3; ++i) {
@@ -107,6 +107,7 @@ lfk::ViewK to_viewk(const lf_view &w, const lf_launch &L)
     k.out_offset = w.out_offset;
     k.tiles_x = (w.width + L.tile_w - 1) / L.tile_w;
     k.tiles_y = (w.height + L.tile_h - 1) / L.tile_h;
+    lfk::fill_view_miss_consts(k, t->desc.radius, t->desc.center);
     return k;
 }
 
@@ -120,7 +121,7 @@ lf_status run_chunk(const lf_table *t, const lfk::RenderParamsBase &base, const 
     const lf_launch &L = t->launch;
     uint64_t tiles = 0;
     for (uint32_t v = 0; v < nv; ++v) {
-        p.views[v] = to_viewk(views[v], L);
+        p.views[v] = to_viewk(views[v], L, t);
         p.tile_prefix[v] = (uint32_t)tiles;
         tiles += (uint64_t)p.views[v].tiles_x * p.views[v].tiles_y;
     }
@@ -197,6 +198,18 @@ size_t code_bytes(int dtype) { return dtype == LF_DTYPE_F32 ? 4 : (dtype == LF_D
 
 namespace lfk {
 void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
+void fill_view_miss_consts(ViewK &k, double R, const double O[3])
+{
+    double f[3] = {(double)k.eye[0] - O[0], (double)k.eye[1] - O[1], (double)k.eye[2] - O[2]};
+    double ff = f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
+    for (int i = 0; i < 3; ++i) k.f0[i] = (float)f[i];
+    k.ff0 = (float)ff;
+    k.c0 = (float)(ff - R * R);
+    k.inv2w = (float)(2.0 / k.width);
+    k.inv2h = (float)(2.0 / k.height);
+    k.outside = (ff - R * R) > 1e-3 * ff ? 1u : 0u;
+}
 
 void fill_sphere_consts(SphereK &S, double R, const double O[3])
 {

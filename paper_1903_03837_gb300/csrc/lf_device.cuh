@@ -112,6 +112,27 @@ __device__ __forceinline__ bool intersect_sphere(const SphereK &S, const float e
     return true;
 }
 
+// True only for rays that certainly miss S: an approximate ray (FMA, no IEEE
+// division) whose line passes outside S, or points away from it, by a
+// relative margin of 1e-4 -- far beyond the ~1e-6 difference between this
+// approximation and the exact FP32 ray, so the exact step would also report a
+// miss. Anything else takes the exact path.
+__device__ __forceinline__ bool certain_miss(const ViewK &v, uint32_t x, uint32_t y)
+{
+    if (!v.outside) return false;
+    float nx = __fmaf_rn(__uint2float_rn(x) + 0.5f, v.inv2w, -1.0f) * v.tan_x;
+    float ny = __fmaf_rn(-(__uint2float_rn(y) + 0.5f), v.inv2h, 1.0f) * v.tan_y;
+    float vx = __fmaf_rn(ny, v.up[0], __fmaf_rn(nx, v.right[0], v.fwd[0]));
+    float vy = __fmaf_rn(ny, v.up[1], __fmaf_rn(nx, v.right[1], v.fwd[1]));
+    float vz = __fmaf_rn(ny, v.up[2], __fmaf_rn(nx, v.right[2], v.fwd[2]));
+    float b = __fmaf_rn(v.f0[0], vx, __fmaf_rn(v.f0[1], vy, v.f0[2] * vz));
+    float vv = __fmaf_rn(vx, vx, __fmaf_rn(vy, vy, vz * vz));
+    float b2 = b * b, vc = vv * v.c0;
+    bool no_disc = (b2 - vc) < -1e-4f * (b2 + vc);
+    bool away = b > 1e-4f * sqrtf(vv * v.ff0);
+    return no_disc || away;
+}
+
 // ---------------------------------------------------------------------------
 // Double-float arithmetic (value = hi + lo, about 48 significant bits).
 // ---------------------------------------------------------------------------

@@ -18,6 +18,10 @@ struct ViewK {
     uint32_t width, height;
     uint64_t out_offset;
     uint32_t tiles_x, tiles_y;
+    // Conservative miss test: e - O, |e - O|^2 - R^2, |e - O|^2, 2/W, 2/H
+    // (host FP64, rounded), and whether the eye is clearly outside S.
+    float f0[3], c0, ff0, inv2w, inv2h;
+    uint32_t outside;
 };
 
 // Sphere S: FP32 centre and radius for the ray/sphere step, the centre as a

@@ -60,6 +60,9 @@ cudaError_t launch_fill_lobe(const LobeParams &P, const float4 *po_hi, const flo
                              const float4 *pd_hi, const float4 *pd_lo, uint32_t M, uint32_t N,
                              float *out, cudaStream_t st);
 
+// Fills the conservative-miss constants of a view for sphere (R, O) (lf_abi.cu).
+void fill_view_miss_consts(ViewK &k, double R, const double O[3]);
+
 // Host-side constants of the sphere used by the unit-hit step: 1/R and R^2 as
 // hi/lo float pairs, 1/R^2, and whether O is the origin (lf_abi.cu).
 void fill_sphere_consts(SphereK &S, double R, const double O[3]);

@@ -69,7 +69,7 @@ lf_status scratch_address(int dev, float4 **out)
 
 template <int MAXV>
 lf_status launch_views(const lfk::RenderParamsBase &base, const lf_launch &L, int kind, int sm_count,
-                       const lf_view *views, uint32_t nv, cudaStream_t st)
+                       const lf_view *views, uint32_t nv, const lf_table_desc *d, cudaStream_t st)
 {
     static thread_local lfk::RenderParams<MAXV> p;
     static_cast<lfk::RenderParamsBase &>(p) = base;
@@ -90,6 +90,7 @@ lf_status launch_views(const lfk::RenderParamsBase &base, const lf_launch &L, in
         k.out_offset = w.out_offset;
         k.tiles_x = (w.width + L.tile_w - 1) / L.tile_w;
         k.tiles_y = (w.height + L.tile_h - 1) / L.tile_h;
+        lfk::fill_view_miss_consts(k, d->radius, d->center);
         p.tile_prefix[v] = (uint32_t)tiles;
         tiles += (uint64_t)k.tiles_x * k.tiles_y;
     }
@@ -224,10 +225,10 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
     b.rows_stored = upper ? M / 2 : 0u;
     int kind = !quant ? (C == 4 ? lfk::kF32C4 : lfk::kF32C3) : (d->dtype == LF_DTYPE_F16 ? lfk::kF16C4 : lfk::kE4M3C4);
     if (n_views <= (uint32_t)lfk::kSmallViews)
-        return launch_views<lfk::kSmallViews>(b, L, kind, sm_count, views, n_views, st);
+        return launch_views<lfk::kSmallViews>(b, L, kind, sm_count, views, n_views, d, st);
     for (uint32_t v0 = 0; v0 < n_views; v0 += lfk::kLargeViews) {
         uint32_t nv = n_views - v0 < (uint32_t)lfk::kLargeViews ? n_views - v0 : (uint32_t)lfk::kLargeViews;
-        s = launch_views<lfk::kLargeViews>(b, L, kind, sm_count, views + v0, nv, st);
+        s = launch_views<lfk::kLargeViews>(b, L, kind, sm_count, views + v0, nv, d, st);
         if (s != LF_OK) return s;
     }
     return LF_OK;

@@ -98,14 +98,25 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
     return true;
 }
 
+// Packed FP32 pair FMA (one instruction for two lanes of a texel).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long *>(&b);
+    unsigned long long rc = *reinterpret_cast<unsigned long long *>(&c);
+    unsigned long long rd;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    return *reinterpret_cast<float2 *>(&rd);
+}
+
 template <int DT>
 __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const ViewK &v, uint32_t px,
                                            uint32_t py)
 {
     int32_t io[5], jd[5];
     float wo[5], wd[5];
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool hit = ray_samples(p, v, px, py, io, jd, wo, wd);
+    float2 acc_xy = make_float2(0.f, 0.f), acc_zw = make_float2(0.f, 0.f);
+    bool hit = !certain_miss(v, px, py) && ray_samples(p, v, px, py, io, jd, wo, wd);
     if (hit) {
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
@@ -114,24 +125,23 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
             float s = wo[a];
             if constexpr (DT == kF16C4 || DT == kE4M3C4) s *= __ldg(p.scales + i);
             size_t row = (size_t)i * p.N;
-            float4 in = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
 #pragma unroll
             for (int b = 0; b < 5; ++b) {
                 float4 t = texel<DT>(p.texels, row + (uint32_t)max(jd[b], 0));
-                in.x = __fmaf_rn(wd[b], t.x, in.x);
-                in.y = __fmaf_rn(wd[b], t.y, in.y);
-                in.z = __fmaf_rn(wd[b], t.z, in.z);
-                in.w = __fmaf_rn(wd[b], t.w, in.w);
+                float2 w2 = make_float2(wd[b], wd[b]);
+                in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
+                in_zw = ffma2(w2, make_float2(t.z, t.w), in_zw);
             }
-            acc.x = __fmaf_rn(s, in.x, acc.x);
-            acc.y = __fmaf_rn(s, in.y, acc.y);
-            acc.z = __fmaf_rn(s, in.z, acc.z);
-            acc.w = __fmaf_rn(s, in.w, acc.w);
+            float2 s2 = make_float2(s, s);
+            acc_xy = ffma2(s2, in_xy, acc_xy);
+            acc_zw = ffma2(s2, in_zw, acc_zw);
         }
     } else {
 #pragma unroll
         for (int a = 0; a < 5; ++a) io[a] = jd[a] = -1;
     }
+    const float4 acc = make_float4(acc_xy.x, acc_xy.y, acc_zw.x, acc_zw.y);
     uint64_t pix = v.out_offset + (uint64_t)py * v.width + px;
     if (p.C == 4) {
         __stcs(reinterpret_cast<float4 *>(p.out) + pix, acc);
@@ -181,7 +191,7 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
     bool hit = false;
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) {
-        hit = ray_samples(p, *v, px, py, io, jd, wo, wd);
+        hit = !certain_miss(*v, px, py) && ray_samples(p, *v, px, py, io, jd, wo, wd);
         uint64_t pix = v->out_offset + (uint64_t)py * v->width + px;
         if (p.C == 4) {
             g = __ldg(reinterpret_cast<const float4 *>(p.grad_out) + pix);

@@ -121,6 +121,8 @@ def _edge_views():
         lf_inputs.look_at((0.2, -3.5, 0.9), (0.1, 0, 0), 13, 7),
         lf_inputs.look_at((1.2, 1.2, 1.2), (0, 0, 0.3), 40, 24),
         lf_inputs.look_at((0.01, 0.0, 5.0), (0, 0, 0), 24, 24),
+        lf_inputs.look_at((0.2, 0.1, 0.3), (1.0, 0.5, 0.0), 20, 20),     # eye inside the sphere
+        lf_inputs.look_at((0.0, 0.0, 3.0), (1.0, 0.0, 0.0), 64, 48),     # silhouette across the image
     ]
     return lf_inputs.pack_offsets(vs)
 
