@@ -161,28 +161,58 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
     }
 }
 
-// Sum of `val` over the lanes of this lane's group `grp` (lanes holding the
-// same texel key), delivered to the group's lowest lane. Every lane of the
-// warp calls this with the same `rounds` = largest group size.
-__device__ __forceinline__ float4 group_sum(float4 val, unsigned grp, int rounds)
+// Position of the n-th (0-based) set bit of m (m has more than n set bits).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n)
 {
-    unsigned rest = grp & (grp - 1u);                 // members after the leader
-    float4 acc = val;
-    for (int r = 1; r < rounds; ++r) {
-        int src = rest ? (__ffs(rest) - 1) : (int)(threadIdx.x & 31);
+    int pos = 0, c;
+    c = __popc(m & 0xffffu); if (n >= c) { n -= c; m >>= 16; pos += 16; }
+    c = __popc(m & 0xffu);   if (n >= c) { n -= c; m >>= 8;  pos += 8; }
+    c = __popc(m & 0xfu);    if (n >= c) { n -= c; m >>= 4;  pos += 4; }
+    c = __popc(m & 0x3u);    if (n >= c) { n -= c; m >>= 2;  pos += 2; }
+    c = (int)(m & 1u);       if (n >= c) { pos += 1; }
+    return pos;
+}
+
+// Sum of `val` over the lanes of this lane's group `grp` (lanes holding the
+// same texel key), delivered to the group's lowest lane: a binary tree over the
+// members' ranks, log2(largest group) rounds. Every lane of the warp calls it.
+__device__ __forceinline__ float4 group_sum_tree(float4 val, unsigned grp, unsigned lane)
+{
+    const int rank = __popc(grp & ((1u << lane) - 1u));
+    const int size = __popc(grp);
+    const int maxsize = (int)__reduce_max_sync(0xffffffffu, (unsigned)size);
+    for (int off = 1; off < maxsize; off <<= 1) {
+        bool recv = (rank & (2 * off - 1)) == 0 && rank + off < size;
+        int src = recv ? nth_set_bit(grp, rank + off) : (int)lane;
         float4 o;
         o.x = __shfl_sync(0xffffffffu, val.x, src);
         o.y = __shfl_sync(0xffffffffu, val.y, src);
         o.z = __shfl_sync(0xffffffffu, val.z, src);
         o.w = __shfl_sync(0xffffffffu, val.w, src);
-        if (rest) {
-            acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
-            rest &= rest - 1u;
+        if (recv) {
+            val.x += o.x; val.y += o.y; val.z += o.z; val.w += o.w;
         }
     }
-    return acc;
+    return val;
 }
 
+__device__ __forceinline__ void add_to_grad(const RenderParamsBase &p, uint64_t key, float4 sum)
+{
+    if (p.C == 4) {
+        atomicAdd(reinterpret_cast<float4 *>(p.grad) + key, sum);
+    } else {
+        float *q = p.grad + key * 3;
+        atomicAdd(q, sum.x);
+        atomicAdd(q + 1, sum.y);
+        atomicAdd(q + 2, sum.z);
+    }
+}
+
+// Backward of one ray: grad[i_a][j_b] += W_ab * g for the 25 taps. Lanes that
+// hold the same texel key are summed first (warp aggregation): when every live
+// lane of the warp has the same key, a butterfly over the warp and one atomic;
+// otherwise __match_any_sync groups and a tree sum per group, one atomic per
+// group. The tap loop stays rolled (instruction-cache footprint).
 __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const ViewK *v, bool active,
                                              uint32_t px, uint32_t py)
 {
@@ -201,27 +231,31 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
         }
     }
     const unsigned lane = threadIdx.x & 31;
+    if (!__any_sync(0xffffffffu, hit)) return;
+#pragma unroll 1
+    for (int t = 0; t < 25; ++t) {
+        const int a = t / 5, b = t - 5 * (t / 5);
+        bool live = hit && (uint32_t)io[a] < p.rows_valid && jd[b] >= 0;
+        uint64_t key = live ? (uint64_t)io[a] * p.N + (uint64_t)jd[b] : 0ull;
+        float W = live ? wo[a] * wd[b] : 0.f;
+        float4 val = make_float4(W * g.x, W * g.y, W * g.z, W * g.w);
+        unsigned live_mask = __ballot_sync(0xffffffffu, live);
+        if (live_mask == 0u) continue;
+        const int leader = __ffs(live_mask) - 1;
+        uint64_t lkey = __shfl_sync(0xffffffffu, key, leader);
+        if (__all_sync(0xffffffffu, !live || key == lkey)) {
 #pragma unroll
-    for (int a = 0; a < 5; ++a) {
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-            bool live = hit && (uint32_t)io[a] < p.rows_valid && jd[b] >= 0;
-            uint64_t key = live ? (uint64_t)io[a] * p.N + (uint64_t)jd[b] : ~0ull - lane;
-            float W = live ? wo[a] * wd[b] : 0.f;
-            float4 val = make_float4(W * g.x, W * g.y, W * g.z, W * g.w);
-            unsigned grp = __match_any_sync(0xffffffffu, key);
-            int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(grp));
-            float4 sum = group_sum(val, grp, rounds);
-            if (live && (__ffs(grp) - 1) == (int)lane) {
-                if (p.C == 4) {
-                    atomicAdd(reinterpret_cast<float4 *>(p.grad) + key, sum);
-                } else {
-                    float *q = p.grad + key * 3;
-                    atomicAdd(q, sum.x);
-                    atomicAdd(q + 1, sum.y);
-                    atomicAdd(q + 2, sum.z);
-                }
+            for (int s = 16; s >= 1; s >>= 1) {
+                val.x += __shfl_xor_sync(0xffffffffu, val.x, s);
+                val.y += __shfl_xor_sync(0xffffffffu, val.y, s);
+                val.z += __shfl_xor_sync(0xffffffffu, val.z, s);
+                val.w += __shfl_xor_sync(0xffffffffu, val.w, s);
             }
+            if ((int)lane == leader) add_to_grad(p, lkey, val);
+        } else {
+            unsigned grp = __match_any_sync(0xffffffffu, live ? key : ~0ull - lane);
+            float4 sum = group_sum_tree(val, grp, lane);
+            if (live && (__ffs(grp) - 1) == (int)lane) add_to_grad(p, key, sum);
         }
     }
 }
