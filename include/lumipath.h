@@ -68,7 +68,7 @@ typedef struct lf_table_desc {
     uint32_t channels;         /* C in {3, 4} */
     int32_t dtype;             /* lf_dtype */
     uint32_t flags;            /* LF_TABLE_* */
-    uint32_t k_nearest;        /* neighbours per hit; 0 means 5; only 5 is supported */
+    uint32_t k_nearest;        /* neighbours per hit: 5 (0 means 5), or 1 for nearest sampling */
 } lf_table_desc;
 
 /* A pinhole camera. Pixel (x, y) of a W x H image looks along
@@ -118,7 +118,8 @@ typedef struct lf_table lf_table;
  *   table; the caller may update their contents between renders (table fitting).
  * Also builds the SF point caches of both sets on `stream`.
  * Errors: LF_ERR_INVALID_ARG (null desc/out/radiance, bad sizes, R <= 0 or
- *   non-finite, missing scales, unsupported channel count, k_nearest != 0/5),
+ *   non-finite, missing scales, unsupported channel count), LF_ERR_UNSUPPORTED
+ *   (k_nearest other than 0, 1 or 5),
  *   LF_ERR_OUT_OF_MEMORY, LF_ERR_CUDA. On error *out is NULL. */
 lf_status lf_create_table(const lf_table_desc *desc, const void *radiance_dev,
                           const float *row_scales_dev, void *stream, lf_table **out);
@@ -127,9 +128,11 @@ lf_status lf_create_table(const lf_table_desc *desc, const void *radiance_dev,
  * views_host: host array of n_views lf_view (read during the call only).
  * out_dev: device FP32 [P][C], P = max(out_offset + W*H) over the views; rays
  *   that miss S get all C channels 0.
- * idx_dev: optional device int32 [P][10]: the 5 origin indices then the 5
+ * idx_dev: optional device int32 [P][2K]: the K origin indices then the K
  *   direction indices of each ray, each set in ascending (squared chord
  *   distance, index) order; -1 for a miss. NULL to skip.
+ * With k_nearest = 1 (nearest sampling, Section 2 and Fig. 2) each hit maps to
+ * its nearest SF point and the pixel takes the single texel L^(i, j).
  * Views must not overlap in the output. n_views <= 65536.
  * Errors: LF_ERR_INVALID_ARG, LF_ERR_CUDA. */
 lf_status lf_render(const lf_table *t, const lf_view *views_host, uint32_t n_views,

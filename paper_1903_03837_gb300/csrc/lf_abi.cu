@@ -180,6 +180,7 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
     b.th_log = (uint32_t)__builtin_ctz(t->launch.tile_h);
     b.ww_log = (uint32_t)__builtin_ctz(t->launch.warp_w);
     b.rows_valid = t->rows;
+    b.nearest_only = t->desc.k_nearest == 1 ? 1u : 0u;
     b.rows_stored = (t->desc.flags & LF_TABLE_UPPER_HEMISPHERE) ? t->rows : 0u;
     const bool bwd = grad != nullptr;
     cudaStream_t st = (cudaStream_t)stream;
@@ -265,8 +266,8 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
     if (C != 3 && C != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4 (got %u)", C);
     if (d->dtype != LF_DTYPE_F32 && d->dtype != LF_DTYPE_F16 && d->dtype != LF_DTYPE_E4M3)
         return fail(LF_ERR_INVALID_ARG, "unknown dtype %d", d->dtype);
-    if (d->k_nearest != 0 && d->k_nearest != 5)
-        return fail(LF_ERR_UNSUPPORTED, "k_nearest=%u: only 5 neighbours per hit are built", d->k_nearest);
+    if (d->k_nearest != 0 && d->k_nearest != 1 && d->k_nearest != 5)
+        return fail(LF_ERR_UNSUPPORTED, "k_nearest=%u: 1 or 5 neighbours per hit are built", d->k_nearest);
     if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
         return fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
     const bool upper = (d->flags & LF_TABLE_UPPER_HEMISPHERE) != 0;

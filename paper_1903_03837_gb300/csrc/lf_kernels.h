@@ -30,6 +30,7 @@ struct RenderParamsBase {
     uint32_t tw_log, th_log, ww_log;   // log2 of tile_w, tile_h, warp_w
     uint32_t rows_stored;              // origin rows present (upper hemisphere), 0: all
     uint32_t rows_valid;               // rows of the table (M or rows_stored)
+    uint32_t nearest_only;             // 1: nearest sampling (K = 1), else 5 neighbours
 };
 
 template <int MAXV>

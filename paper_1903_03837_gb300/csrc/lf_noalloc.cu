@@ -142,8 +142,8 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
     const bool quant = d->dtype != LF_DTYPE_F32;
     if (quant && (C != 4 || !row_scales_dev))
         return na_fail(LF_ERR_INVALID_ARG, "F16/E4M3 tables need 4 channels and row scales here");
-    if (d->k_nearest != 0 && d->k_nearest != 5)
-        return na_fail(LF_ERR_UNSUPPORTED, "only 5 neighbours per hit are built");
+    if (d->k_nearest != 0 && d->k_nearest != 1 && d->k_nearest != 5)
+        return na_fail(LF_ERR_UNSUPPORTED, "1 or 5 neighbours per hit are built");
     if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
         return na_fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
     if ((d->flags & LF_TABLE_UPPER_HEMISPHERE) && M < 2)
@@ -222,6 +222,7 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
     b.ww_log = (uint32_t)__builtin_ctz(L.warp_w);
     const bool upper = (d->flags & LF_TABLE_UPPER_HEMISPHERE) != 0;
     b.rows_valid = upper ? M / 2 : M;
+    b.nearest_only = d->k_nearest == 1 ? 1u : 0u;
     b.rows_stored = upper ? M / 2 : 0u;
     int kind = !quant ? (C == 4 ? lfk::kF32C4 : lfk::kF32C3) : (d->dtype == LF_DTYPE_F16 ? lfk::kF16C4 : lfk::kE4M3C4);
     if (n_views <= (uint32_t)lfk::kSmallViews)

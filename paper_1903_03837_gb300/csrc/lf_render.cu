@@ -76,7 +76,14 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
         P.inv_sigma = s ? p.pd.inv_sigma : p.po.inv_sigma;
         Top5 r = knn5(P, p.sphere, s ? hd : ho, p.status);
         float w[5];
-        if (s == 0 && p.rows_stored) {
+        if (p.nearest_only) {
+            // nearest sampling: the nearest point alone (Section 2, Fig. 2)
+            if (s == 0 && p.rows_stored && (uint32_t)r.i[0] >= p.rows_stored) return false;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) w[m] = m == 0 ? 1.0f : 0.0f;
+#pragma unroll
+            for (int m = 1; m < 5; ++m) r.i[m] = -1;
+        } else if (s == 0 && p.rows_stored) {
             if (!tent_weights_kept(r.d2, r.i, r.cnt, P.inv_sigma, p.rows_stored, w)) return false;
         } else {
             tent_weights(r.d2, r.cnt, P.inv_sigma, w);
@@ -118,8 +125,10 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
     float2 acc_xy = make_float2(0.f, 0.f), acc_zw = make_float2(0.f, 0.f);
     bool hit = !certain_miss(v, px, py) && ray_samples(p, v, px, py, io, jd, wo, wd);
     if (hit) {
+        const int taps = p.nearest_only ? 1 : 5;
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
+            if (a >= taps) break;
             // a missing or unstored neighbour has weight 0 and reads row 0
             int32_t i = (uint32_t)io[a] < p.rows_valid ? io[a] : 0;
             float s = wo[a];
@@ -128,6 +137,7 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
             float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
 #pragma unroll
             for (int b = 0; b < 5; ++b) {
+                if (b >= taps) break;
                 float4 t = texel<DT>(p.texels, row + (uint32_t)max(jd[b], 0));
                 float2 w2 = make_float2(wd[b], wd[b]);
                 in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
@@ -152,12 +162,16 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
         __stcs(o + 2, acc.z);
     }
     if (p.idx) {
-        int2 *q = reinterpret_cast<int2 *>(p.idx + pix * 10);
-        q[0] = make_int2(io[0], io[1]);
-        q[1] = make_int2(io[2], io[3]);
-        q[2] = make_int2(io[4], jd[0]);
-        q[3] = make_int2(jd[1], jd[2]);
-        q[4] = make_int2(jd[3], jd[4]);
+        if (p.nearest_only) {
+            reinterpret_cast<int2 *>(p.idx)[pix] = make_int2(io[0], jd[0]);
+        } else {
+            int2 *q = reinterpret_cast<int2 *>(p.idx + pix * 10);
+            q[0] = make_int2(io[0], io[1]);
+            q[1] = make_int2(io[2], io[3]);
+            q[2] = make_int2(io[4], jd[0]);
+            q[3] = make_int2(jd[1], jd[2]);
+            q[4] = make_int2(jd[3], jd[4]);
+        }
     }
 }
 

@@ -41,7 +41,7 @@ class LightField:
 
     def __init__(self, radiance: torch.Tensor, dtype: str = "f32", scales: Optional[torch.Tensor] = None,
                  R: float = 1.0, O=(0.0, 0.0, 0.0), borrow: bool = False, n_origins: Optional[int] = None,
-                 upper: bool = False):
+                 upper: bool = False, k_nearest: int = 5):
         _need_cuda(radiance, "radiance")
         if radiance.dim() != 3:
             raise ValueError("radiance must be [M, N, C]")
@@ -61,7 +61,8 @@ class LightField:
         desc.n_origins, desc.n_directions, desc.channels = M, N, Cc
         desc.dtype = lp.DTYPES[dtype]
         desc.flags = (lp.LF_TABLE_BORROW if borrow else 0) | (lp.LF_TABLE_UPPER_HEMISPHERE if upper else 0)
-        desc.k_nearest = 5
+        desc.k_nearest = int(k_nearest)
+        self.K = int(k_nearest)
         self.M, self.N, self.C, self.dtype, self.R, self.O = M, N, Cc, dtype, float(R), tuple(O)
         self.rows, self.upper = rows, bool(upper)
         self._keep = (radiance, scales) if borrow else None
@@ -86,11 +87,11 @@ class LightField:
         if out.numel() < P * self.C or out.dtype != torch.float32:
             raise ValueError("out must be float32 with at least P*C elements")
         if with_idx and idx is None:
-            idx = torch.empty((P, 10), dtype=torch.int32, device="cuda")
+            idx = torch.empty((P, 2 * self.K), dtype=torch.int32, device="cuda")
         if idx is not None:
             _need_cuda(idx, "idx")
-            if idx.numel() < P * 10 or idx.dtype != torch.int32:
-                raise ValueError("idx must be int32 with at least P*10 elements")
+            if idx.numel() < P * 2 * self.K or idx.dtype != torch.int32:
+                raise ValueError("idx must be int32 with at least P*2K elements")
         vv = lp.make_views(views)
         lp.lf_render(self.handle, vv, len(views), out.data_ptr(), idx.data_ptr() if idx is not None else None,
                      _stream())

@@ -374,3 +374,22 @@ def test_upper_hemisphere_table(api, dtype):
                                 g.cpu().numpy()[offs].astype(np.float64))
     assert np.abs(G - Gw).max() <= 2e-5 * max(1.0, np.abs(Gw).max())
     lf.close()
+
+
+@pytest.mark.parametrize("M,N,upper", [(1024, 256, False), (65536, 1024, False), (3001, 700, True)])
+def test_nearest_sampling_mode(api, M, N, upper):
+    """k_nearest = 1: each hit takes its nearest SF point and the pixel the single
+    texel L^(i, j) (Section 2, nearest sampling)."""
+    rng = np.random.default_rng(M + N)
+    rows = M // 2 if upper else M
+    T = rng.uniform(0, 1, (rows, N, 4)).astype(np.float32)
+    views = lf_inputs.pack_offsets([lf_inputs.look_at((2.4, 0.3, 0.4), (0, 0, 0), 96, 80),
+                                    lf_inputs.look_at((0.2, 0.1, 2.6), (0, 0, 0), 40, 40)])
+    want_out, want_idx, hits = oracle.render_views(oracle.Scene(M, N, 4, "f32", T, K=1, upper=upper), views)
+    lf = api.LightField(torch.from_numpy(T).cuda(), "f32", n_origins=M, upper=upper, k_nearest=1)
+    out, idx = lf.render(views, with_idx=True)
+    lf.sync_status()
+    got = (out.cpu().numpy(), idx.cpu().numpy())
+    assert got[1].shape == (lf_inputs.total_pixels(views), 2)
+    check_parity(got, (want_out, want_idx))
+    lf.close()
