@@ -54,6 +54,38 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def csrc_digest() -> str:
+    """SHA-256 over the CUDA sources of the library (name + content, sorted)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1903_03837_gb300", "csrc")
+    h = hashlib.sha256()
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh", ".h")):
+            h.update(n.encode())
+            with open(os.path.join(d, n), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(dtype: str):
+    """DRAM bytes (read + write) per launch of the render kernel on this workload,
+    from the ncu launch list summarised in profiles/render_traffic.txt; None when
+    the kernel sources have changed since that capture."""
+    p = os.path.join(ROOT, "profiles", "render_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    rec = {}
+    with open(p) as f:
+        for ln in f:
+            parts = ln.split()
+            if len(parts) == 2 and not ln.startswith("#"):
+                rec[parts[0]] = parts[1]
+    if rec.get("csrc_sha256") != csrc_digest():
+        return None
+    v = rec.get(f"{dtype}_dram_bytes_per_launch")
+    return int(v) if v else None
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -276,7 +308,7 @@ def run_ours(args, rank: int, world: int):
                    "launch": launch, "parallelism": f"replicas x{world} (views sharded, no collective)",
                    "setup_s": round(setup_s, 2)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": recorded_traffic(args.dtype),
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "kernel": f"lfk::render_kernel<{args.dtype}>", "avg_launch_ms": avg_launch_s * 1e3},
@@ -297,6 +329,8 @@ def run_ours(args, rank: int, world: int):
         line["fit"] = run_fit_steps(args)
         torch.cuda.empty_cache()
         line["paper_shape"] = run_paper_shape(args)
+        torch.cuda.empty_cache()
+        line["batching"] = run_batching(args)
         tables = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "large":
         line["cpu_baseline"], psnr64 = cpu_baseline(cfg, frame_views[f0], gpu_images, args)
@@ -354,6 +388,49 @@ def run_fit_steps(args):
             "ms_per_fit_step": ms, "fit_steps_per_s": 1e3 / ms,
             "backward_ms": bms, "backward_grays_s": rays / (bms * 1e-3) / 1e9,
             "fwd_bwd_adam_grays_s": rays / (ms * 1e-3) / 1e9}
+
+
+def run_batching(args):
+    """Batching workload: 16,384 x 512 RGBA FP16 table, 64 views of uneven size
+    (16 stereo pairs of 1440x1600, 256x256, 2048x1080, 30 random multiples of 8)
+    rendered in one persistent launch that a CUDA graph replays; the autotuner
+    picks tile shape and ray order for the persistent grid."""
+    import torch
+    from paper_1903_03837_gb300 import torch_api as api, autotune
+    cfg = lf_inputs.config_batching()
+    T32 = api.fill_lobe_table(cfg.lobes(), cfg.M, cfg.N)
+    codes, s = api.quantize_table(T32, "f16")
+    del T32
+    lf = api.LightField(codes, "f16", s, borrow=True)
+    persistent = [c for c in autotune.CANDIDATES if c[4] == 1]
+    ranked = autotune.tune(lf, [cfg.views], persistent, reps=2)
+    launch = ranked[0][1]
+    lf.set_launch(**launch)
+    out = torch.empty((cfg.rays, 4), device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        lf.render(cfg.views, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        lf.render(cfg.views, out=out)
+    for _ in range(args.warmup):
+        graph.replay()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(args.steps):
+        graph.replay()
+    b.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    lf.close()
+    return {"workload": f"batching: {cfg.M:,} x {cfg.N:,} RGBA FP16 table, {len(cfg.views)} views of uneven "
+                        f"size ({cfg.rays:,} rays) in one persistent launch replayed from a CUDA graph",
+            "launch": launch, "ms_per_batch": ms, "grays_s": cfg.rays / (ms * 1e-3) / 1e9,
+            "autotune_top3_ms": [round(r[0], 4) for r in ranked[:3]]}
 
 
 def run_paper_shape(args):
