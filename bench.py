@@ -281,13 +281,19 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    t_e2e = time.perf_counter()
-    for k in range(args.steps):
-        e2e_frame(k, my_frames[args.warmup + k])
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t_e2e
-    if world > 1:
-        e2e_s = replicas.reduce_max(e2e_s)
+    # Three timed windows of K frames each; the median is reported (the
+    # device-to-host copies share the host's memory system with other work).
+    e2e_windows = []
+    for _ in range(3):
+        t_e2e = time.perf_counter()
+        for k in range(args.steps):
+            e2e_frame(k, my_frames[args.warmup + k])
+        torch.cuda.synchronize()
+        w_s = time.perf_counter() - t_e2e
+        if world > 1:
+            w_s = replicas.reduce_max(w_s)
+        e2e_windows.append(w_s)
+    e2e_s = sorted(e2e_windows)[1]
 
     peak, peak_kind = measured_peaks()
     avg_launch_s = sum(per_ms) / len(per_ms) * 1e-3
@@ -316,7 +322,9 @@ def run_ours(args, rank: int, world: int):
         "e2e": {"value": world * args.steps * rays / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 72, "d2h_bytes_per_step": rays * 16,
                 "how": "lf_render per frame with host lf_view structs, image copied to pinned host "
-                       "memory every frame on a second stream (double-buffered)"},
+                       "memory every frame on a second stream (double-buffered); median of 3 "
+                       "windows of K frames",
+                "windows_grays_s": [world * args.steps * rays / w / 1e9 for w in e2e_windows]},
         "gpu_launches": args.steps,
         "variants": variants,
         "psnr_vs_f32_table_db": psnr_vs_f32,
@@ -544,8 +552,9 @@ def main():
     ap.add_argument("--quick-tune", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--launch", default="", help="tile_w,tile_h,warp_w,order,persistent (skips the autotuner)")
-    ap.add_argument("--workload", default="large", choices=["large", "precision"],
-                    help="precision: 65,536 x 1,024 table, one 1920x1080 view (small profiling case)")
+    ap.add_argument("--workload", default="large", choices=["large", "precision", "fit"],
+                    help="precision: 65,536 x 1,024 table, one 1920x1080 view (small profiling case); "
+                         "fit: the differentiation leg alone (forward + backward + Adam per step)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -555,6 +564,11 @@ def main():
         if rank != 0:
             return
         print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if args.workload == "fit":
+        # profiling case for the backward kernel: one JSON object, rank 0 only
+        if rank == 0:
+            print(json.dumps({"fit": run_fit_steps(args)}), flush=True)
         return
     if world > 1:
         import torch

@@ -275,11 +275,15 @@ __device__ __forceinline__ double dist2_fp64(const PointSetK &P, int32_t i, cons
 //          (u, v) are the hit's coordinates in the local Fibonacci basis of zone k.
 // Tier 1 ranks every candidate by an FP32 squared distance from the hi parts
 // only (key = float bits with the low bits replaced by the slot) and keeps the
-// 7 smallest keys. With the rigorous error bound e1 of that distance, the true
-// 5 nearest lie among the tier-1 top 6 when the 5th key's upper bound is below
-// the 7th key's lower bound. Tier 2 recomputes those 6 in double-float, sorts
-// them and accepts the order when every consecutive gap exceeds the tier-2
-// error. Anything uncertain is ranked again in FP64 by (distance, index).
+// 7 smallest keys. With the rigorous error bound e1 of that distance, the
+// tier-1 order of the top 5 is the exact one when each of the top 6 keys'
+// upper bound lies below the next key's lower bound (by more than an FP64
+// rounding): the common case, which needs double-float distances of those 5
+// only (for the weights). Otherwise the true 5 nearest still lie among the
+// tier-1 top 6 when the 5th key's upper bound is below the 7th key's lower
+// bound; tier 2 recomputes those 6 in double-float, sorts them and accepts the
+// order when every consecutive gap exceeds the tier-2 error. Anything
+// uncertain is ranked again in FP64 by (distance, index).
 // ---------------------------------------------------------------------------
 #define LF_CS(a, b)                          \
     {                                        \
@@ -515,50 +519,85 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
             insert7(s7, (__float_as_uint(dist2_hi(P, src.scan_base + s, qh)) & ~mask1) | (uint32_t)s);
     }
 
-    // Membership: 5th upper bound below the 7th lower bound.
-    bool exact = true;
-    if (s7[6] != kNone) {
-        float a = __uint_as_float(s7[4] & ~mask1), b = __uint_as_float(s7[6] & ~mask1);
-        float pack = __uint_as_float(s7[4] | mask1) - a;
-        exact = (b - tier1_err(b)) > (a + pack + tier1_err(a + pack));
-    }
-
-    // Tier 2: double-float distances of the top 6, sorted; 3 slot bits.
-    uint32_t k6[6];
-    int32_t id6[6];
+    // Bounds of the exact squared distance behind each of the 7 keys: the key
+    // lost its low `bits` bits to the slot, and one FP32 error bound serves
+    // all 7 (tier1_err grows with the distance; taken at the 7th key, and at
+    // 4.5 > any squared chord when that slot is empty).
+    float ub[7], lb[7];
+    const float e7 = tier1_err(fminf(__uint_as_float(s7[6] | mask1), 4.5f));
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-        bool ok = s7[m] != kNone;
-        int32_t i = ok ? source_index(src, (int)(s7[m] & mask1)) : 0;
-        id6[m] = i;
-        float dd = dist2_df(P, i, qh, ql);
-        k6[m] = ok ? ((__float_as_uint(dd) & ~7u) | (uint32_t)m) : kNone;
+    for (int m = 0; m < 7; ++m) {
+        ub[m] = __uint_as_float(s7[m] | mask1) + e7;
+        lb[m] = __uint_as_float(s7[m] & ~mask1) - e7;
     }
-    sort6(k6);
-    // Order among the 5 and the 5th/6th boundary at tier-2 precision.
+    // Double-float distances of the tier-1 top 5 (the weights need them).
+    int32_t i5[5];
+    float p5[5];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        if (k6[m + 1] != kNone) {
-            float a = __uint_as_float(k6[m] & ~7u), b = __uint_as_float(k6[m + 1] & ~7u);
-            exact &= (b - a) > __fmaf_rn(0x1p-18f, b, 0x1p-40f);
-        }
+        bool ok = s7[m] != kNone;
+        i5[m] = ok ? source_index(src, (int)(s7[m] & mask1)) : 0;
+        p5[m] = dist2_df(P, i5[m], qh, ql);
     }
+    // Order certificate at tier 1: each of the top 6 lies strictly below the
+    // next by more than any FP64 rounding of the ranking distances (2^-40), so
+    // order and membership of the 5 equal those of the exact ranking. Else
+    // tier 2 re-ranks the top 6 in double-float, and FP64 settles the rest.
+    bool order1 = true;
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+        if (s7[m + 1] != kNone) order1 &= (lb[m + 1] - ub[m]) > 0x1p-40f;
     Top5 r;
-    if (exact) {
-        r.cnt = 0;
+    r.cnt = 0;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        bool ok = s7[m] != kNone;
+        r.i[m] = ok ? i5[m] : -1;
+        r.d2[m] = ok ? p5[m] : 0.0f;
+        r.cnt += ok ? 1 : 0;
+    }
+    if (!order1) {
+        // membership: the 5th upper bound below the 7th lower bound
+        bool exact = s7[6] == kNone || lb[6] > ub[4];
+        uint32_t k6[6];
+        int32_t id6[6];
+        float dd6[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            bool ok = s7[m] != kNone;
+            int32_t i = m < 5 ? i5[m] : (ok ? source_index(src, (int)(s7[m] & mask1)) : 0);
+            id6[m] = i;
+            dd6[m] = m < 5 ? p5[m] : dist2_df(P, i, qh, ql);
+            k6[m] = ok ? ((__float_as_uint(dd6[m]) & ~7u) | (uint32_t)m) : kNone;
+        }
+        sort6(k6);
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            bool ok = k6[m] != kNone;
-            int sl = (int)(k6[m] & 7u);
-            int32_t i = id6[0];
-#pragma unroll
-            for (int c = 1; c < 6; ++c) i = (sl == c) ? id6[c] : i;
-            r.i[m] = ok ? i : -1;
-            r.d2[m] = ok ? __uint_as_float(k6[m] & ~7u) : 0.0f;
-            r.cnt += ok ? 1 : 0;
+            if (k6[m + 1] != kNone) {
+                float a = __uint_as_float(k6[m] & ~7u), b = __uint_as_float(k6[m + 1] & ~7u);
+                exact &= (b - a) > __fmaf_rn(0x1p-18f, b, 0x1p-40f);
+            }
         }
-    } else {
-        r = knn5_fp64(P, S, h, src, qh, ql);
+        if (exact) {
+            r.cnt = 0;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                bool ok = k6[m] != kNone;
+                int sl = (int)(k6[m] & 7u);
+                int32_t i = id6[0];
+                float dd = dd6[0];
+#pragma unroll
+                for (int c = 1; c < 6; ++c) {
+                    i = (sl == c) ? id6[c] : i;
+                    dd = (sl == c) ? dd6[c] : dd;
+                }
+                r.i[m] = ok ? i : -1;
+                r.d2[m] = ok ? dd : 0.0f;
+                r.cnt += ok ? 1 : 0;
+            }
+        } else {
+            r = knn5_fp64(P, S, h, src, qh, ql);
+        }
     }
 #pragma unroll
     for (int m = 0; m < 5; ++m) {

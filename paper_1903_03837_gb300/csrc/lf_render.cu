@@ -14,8 +14,10 @@
 #include "lf_device.cuh"
 #include "lf_kernels.h"
 
+// Resident CTAs of kMaxBlock threads per SM the register budget is cut for:
+// 4 -> 64 registers, 32 warps per SM (forward and backward).
 #ifndef LF_MIN_BLOCKS
-#define LF_MIN_BLOCKS 3
+#define LF_MIN_BLOCKS 4
 #endif
 
 namespace lfk {
@@ -62,6 +64,10 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
                                             uint32_t py, int32_t io[5], int32_t jd[5], float wo[5],
                                             float wd[5])
 {
+    // The origin set's indices and weights wait in shared memory (one slot per
+    // thread, no synchronisation) while the direction set is searched: ten
+    // fewer live registers across the second search.
+    __shared__ int s_stash[10 * kMaxBlock];
     float3 d = camera_dir(v, px, py);
     float3 ho, hd;
     if (!intersect_sphere(p.sphere, v.eye, d, ho, hd)) return false;
@@ -91,8 +97,8 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
         if (s == 0) {
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
-                io[m] = r.i[m];
-                wo[m] = w[m];
+                s_stash[m * kMaxBlock + threadIdx.x] = r.i[m];
+                s_stash[(5 + m) * kMaxBlock + threadIdx.x] = __float_as_int(w[m]);
             }
         } else {
 #pragma unroll
@@ -101,6 +107,11 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
                 wd[m] = w[m];
             }
         }
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        io[m] = s_stash[m * kMaxBlock + threadIdx.x];
+        wo[m] = __int_as_float(s_stash[(5 + m) * kMaxBlock + threadIdx.x]);
     }
     return true;
 }
@@ -125,10 +136,11 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
     float2 acc_xy = make_float2(0.f, 0.f), acc_zw = make_float2(0.f, 0.f);
     bool hit = !certain_miss(v, px, py) && ray_samples(p, v, px, py, io, jd, wo, wd);
     if (hit) {
-        const int taps = p.nearest_only ? 1 : 5;
+        // All 25 taps in every mode: with nearest sampling the other 24 have
+        // weight 0 and index -1 (row 0, texel 0, an L1 hit), which costs less
+        // than a second copy of the loop.
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
-            if (a >= taps) break;
             // a missing or unstored neighbour has weight 0 and reads row 0
             int32_t i = (uint32_t)io[a] < p.rows_valid ? io[a] : 0;
             float s = wo[a];
@@ -137,7 +149,6 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
             float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
 #pragma unroll
             for (int b = 0; b < 5; ++b) {
-                if (b >= taps) break;
                 float4 t = texel<DT>(p.texels, row + (uint32_t)max(jd[b], 0));
                 float2 w2 = make_float2(wd[b], wd[b]);
                 in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
