@@ -294,6 +294,13 @@ def run_ours(args, rank: int, world: int):
             w_s = replicas.reduce_max(w_s)
         e2e_windows.append(w_s)
     e2e_s = sorted(e2e_windows)[1]
+    # The link's ceiling for this metric: the same device-to-host copy alone.
+    torch.cuda.synchronize()
+    t_cp = time.perf_counter()
+    for k in range(5):
+        host[k % 2].copy_(outs[k % 2], non_blocking=True)
+    torch.cuda.synchronize()
+    d2h_gbs = 5 * rays * 16 / (time.perf_counter() - t_cp) / 1e9
 
     peak, peak_kind = measured_peaks()
     avg_launch_s = sum(per_ms) / len(per_ms) * 1e-3
@@ -324,7 +331,8 @@ def run_ours(args, rank: int, world: int):
                 "how": "lf_render per frame with host lf_view structs, image copied to pinned host "
                        "memory every frame on a second stream (double-buffered); median of 3 "
                        "windows of K frames",
-                "windows_grays_s": [world * args.steps * rays / w / 1e9 for w in e2e_windows]},
+                "windows_grays_s": [world * args.steps * rays / w / 1e9 for w in e2e_windows],
+                "d2h_copy_gbs": d2h_gbs, "copy_bound_grays_s": world * d2h_gbs * 1e9 / (rays * 16) / 1e9},
         "gpu_launches": args.steps,
         "variants": variants,
         "psnr_vs_f32_table_db": psnr_vs_f32,
