@@ -137,6 +137,48 @@ def draw_lobes(seed: int, L: int, C: int) -> Lobes:
                  np.ascontiguousarray(col), noise_seed=int(seed))
 
 
+@dataclass
+class Volume:
+    """An analytic emission-absorption scene inside S for the light-field
+    precompute: Gaussian blobs (centre, width, peak density per unit length,
+    emitted RGB colour), a direction-only background bg0 + bg1 (1 + d_z) / 2,
+    and the sampling controls (jittered samples per texel, midpoint steps per
+    sample, generator seed)."""
+    mu: np.ndarray      # [B,3] centres
+    width: np.ndarray   # [B]
+    dens: np.ndarray    # [B]
+    emit: np.ndarray    # [B,3]
+    bg0: Tuple[float, float, float] = (0.02, 0.02, 0.03)
+    bg1: Tuple[float, float, float] = (0.10, 0.12, 0.20)
+    spp: int = 4
+    steps: int = 64
+    jitter: int = 1
+    seed: int = 0
+    R: float = 1.0
+    O: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+
+    @property
+    def B(self) -> int:
+        return len(self.width)
+
+
+def draw_volume(seed: int, B: int = 8, R: float = 1.0, O=(0.0, 0.0, 0.0), spp: int = 4,
+                steps: int = 64, jitter: int = 1) -> Volume:
+    """B blobs: centres uniform in the ball of radius 0.6R around O, widths
+    U[0.08, 0.25]R, peak densities U[2, 12]/R, colours U[0, 1]^3."""
+    rng = np.random.default_rng(seed + 7000)
+    u = rng.standard_normal((B, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    rad = 0.6 * R * rng.uniform(0.0, 1.0, B) ** (1.0 / 3.0)
+    mu = np.asarray(O, np.float64)[None, :] + u * rad[:, None]
+    width = rng.uniform(0.08, 0.25, B) * R
+    dens = rng.uniform(2.0, 12.0, B) / R
+    emit = rng.uniform(0.0, 1.0, (B, 3))
+    return Volume(np.ascontiguousarray(mu), np.ascontiguousarray(width), np.ascontiguousarray(dens),
+                  np.ascontiguousarray(emit), spp=spp, steps=steps, jitter=jitter, seed=int(seed),
+                  R=float(R), O=tuple(float(x) for x in O))
+
+
 # --------------------------------------------------------------------------
 # Workloads
 # --------------------------------------------------------------------------
@@ -207,6 +249,17 @@ def config_differentiation(seed: int = 0, n_train: int = 32, n_held: int = 8) ->
                          "fd_M": 256, "fd_N": 64})
 
 
+def config_precompute(seed: int = 0) -> Config:
+    """Light-field precompute of an analytic volume scene (8 Gaussian blobs,
+    4 jittered samples per texel, 64 midpoint steps) into a 16,384 x 512 RGBA
+    FP32 table (the size of the differentiation table), rendered from the
+    differentiation workload's 8 held-out views."""
+    d = config_differentiation(seed)
+    views = pack_offsets(d.views[-8:])
+    return Config("precompute", 16384, 512, 4, 8, seed, ("f32",), views,
+                  extra={"volume": draw_volume(seed, B=8)})
+
+
 def orbit_frame(f: int, frames: int = 240, dist: float = 3.0, elev_deg: float = 20.0,
                 width: int = 3840, height: int = 2160, R: float = 1.0) -> List[View]:
     """Frame f of the orbit: centre at distance `dist`, elevation 20 degrees,
@@ -242,6 +295,7 @@ CONFIGS = {
     "differentiation": config_differentiation,
     "large": config_large,
     "paper": config_paper,
+    "precompute": config_precompute,
 }
 
 

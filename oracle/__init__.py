@@ -18,6 +18,9 @@ marshals numpy arrays through ctypes. Functions:
 * ``render_backward``                        -- adjoint of the blend w.r.t. the table
 * ``f16_*``, ``e4m3_*``, ``quantize_rows``   -- per-row FP16 / E4M3 table storage
 * ``lobe_table``                             -- the synthetic lobe radiance field
+* ``volume_table``, ``volume_ray``, ``volume_origin`` -- light-field precompute (Section 3):
+  every ray r_k through an emission-absorption volume of Gaussian blobs, origins
+  jittered on the disk of area A_S/M
 * ``psnr``                                   -- image error against an FP64 render
 
 Parity unpinned: none. Each function is pinned in ``tests/test_oracle_pins.py``.
@@ -96,6 +99,11 @@ def lib():
                 "lfo_render_pixels": (i64, [vp, vp, vp, vp, i64, vp, vp]),
                 "lfo_render_backward_pixels": (None, [vp, vp, vp, vp, i64, vp, vp]),
                 "lfo_trace_pixel": (C.c_int, [dbl, vp, vp, u32, u32, u32, u32, vp, vp, vp, vp, vp]),
+                "lfo_volume_origin": (None, [vp, u32, u32, vp, u32, u32, u32, vp]),
+                "lfo_volume_tend": (dbl, [vp, vp, vp]),
+                "lfo_volume_ray": (None, [vp, vp, vp, vp, vp]),
+                "lfo_volume_texel": (None, [vp, vp, vp, u32, u32, u32, u32, vp]),
+                "lfo_volume_table_rows": (None, [vp, vp, vp, u32, u32, u32, u32, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -288,6 +296,79 @@ def lobe_table(lobes, M: int, N: int, rows: Optional[Sequence[int]] = None,
 
     def one(k):
         L.lfo_lobe_table_rows(C.byref(h.s), _p(Po), _p(Pd), N, rows[k], rows[k] + 1, _p(out[k:]))
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, range(len(rows))))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Light-field precompute (Section 3): volume scene
+# --------------------------------------------------------------------------
+class _Volume(C.Structure):
+    _fields_ = [("B", C.c_uint32), ("C", C.c_uint32), ("spp", C.c_uint32), ("steps", C.c_uint32),
+                ("jitter", C.c_uint32), ("pad_", C.c_uint32), ("seed", C.c_uint64),
+                ("R", C.c_double), ("O", C.c_double * 3), ("mu", C.c_void_p), ("width", C.c_void_p),
+                ("dens", C.c_void_p), ("emit", C.c_void_p), ("bg0", C.c_double * 3),
+                ("bg1", C.c_double * 3)]
+
+
+class _VolumeHold:
+    """ctypes view of a volume scene (any object with mu [B,3], width [B],
+    dens [B], emit [B,3], bg0 [3], bg1 [3], spp, steps, jitter, seed, R, O)."""
+
+    def __init__(self, vol, C_: int):
+        self.mu = np.ascontiguousarray(np.asarray(vol.mu, np.float64).reshape(-1, 3))
+        self.width = np.ascontiguousarray(vol.width, np.float64)
+        self.dens = np.ascontiguousarray(vol.dens, np.float64)
+        self.emit = np.ascontiguousarray(np.asarray(vol.emit, np.float64).reshape(-1, 3))
+        B = len(self.width)
+        self.s = _Volume(B, C_, int(vol.spp), int(vol.steps), int(vol.jitter), 0,
+                         int(vol.seed) & (2**64 - 1), float(vol.R), (C.c_double * 3)(*vol.O),
+                         _p(self.mu).value if B else None, _p(self.width).value if B else None,
+                         _p(self.dens).value if B else None, _p(self.emit).value if B else None,
+                         (C.c_double * 3)(*vol.bg0), (C.c_double * 3)(*vol.bg1))
+
+
+def volume_origin(vol, M: int, N: int, i: int, j: int, s: int) -> np.ndarray:
+    """Origin of sample s of texel (i, j) (on the tangent disk of area 4 pi R^2 / M)."""
+    h = _VolumeHold(vol, 3)
+    o = np.zeros(3)
+    lib().lfo_volume_origin(C.byref(h.s), M, N, _p(np.ascontiguousarray(sf_point(M, i))), i, j, s, _p(o))
+    return o
+
+
+def volume_ray(vol, o, d):
+    """(rgb [3], final transmittance, t_end) of one ray through the volume."""
+    h = _VolumeHold(vol, 3)
+    o = np.ascontiguousarray(o, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    rgb, T = np.zeros(3), C.c_double()
+    lib().lfo_volume_ray(C.byref(h.s), _p(o), _p(d), _p(rgb), C.byref(T))
+    return rgb, T.value, float(lib().lfo_volume_tend(C.byref(h.s), _p(o), _p(d)))
+
+
+def volume_table(vol, M: int, N: int, C_: int = 4, rows: Optional[Sequence[int]] = None,
+                 texels: Optional[np.ndarray] = None, threads: Optional[int] = None) -> np.ndarray:
+    """FP32 precomputed table [M,N,C] (or [len(rows),N,C]); with `texels`
+    ([K,2] array of (i, j)), FP64 values of those texels [K,C] instead."""
+    h = _VolumeHold(vol, C_)
+    Po, Pd = sf_points(M), sf_points(N)
+    L = lib()
+    if texels is not None:
+        texels = np.asarray(texels, np.int64).reshape(-1, 2)
+        out = np.zeros((len(texels), 4))
+
+        def one_t(k):
+            L.lfo_volume_texel(C.byref(h.s), _p(Po), _p(Pd), M, N, int(texels[k, 0]), int(texels[k, 1]),
+                               _p(out[k:]))
+        with ThreadPoolExecutor(_threads(threads)) as ex:
+            list(ex.map(one_t, range(len(texels))))
+        return out[:, :C_].copy()
+    rows = list(range(M)) if rows is None else [int(r) for r in rows]
+    out = np.zeros((len(rows), N, C_), np.float32)
+
+    def one(k):
+        L.lfo_volume_table_rows(C.byref(h.s), _p(Po), _p(Pd), M, N, rows[k], rows[k] + 1, _p(out[k:]))
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(one, range(len(rows))))
     return out

@@ -22,6 +22,9 @@
  *   - the adjoint of that blend with respect to the table (gradient of a linear map).
  *   - the synthetic lobe radiance field used as input, and the FP16 / FP8-E4M3
  *     per-row quantisers written from the IEEE 754 binary16 and OCP E4M3FN definitions.
+ *   - the light-field precompute (Section 3, equation of r_k; origins jittered on a
+ *     disk of area A_S/M): every ray r_k traced through an analytic emission-absorption
+ *     volume (Gaussian blobs), midpoint rule, mean over jittered samples.
  *
  * Everything that decides a neighbour is FP64; the camera ray and the sphere
  * intersection are FP32 with one fixed operation order and no contraction
@@ -468,4 +471,140 @@ int lfo_trace_pixel(double R, const double O[3], const float *vw, uint32_t W, ui
     lfo_normalize_hit(ho, O, qo);
     lfo_normalize_hit(hd, O, qd);
     return 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Light-field precompute (Section 3): L^(i,j) is the radiance a camera ray   */
+/* r_k = (O + R p^o_i) + t d_ij, d_ij = (p^d_j - p^o_i)/|p^d_j - p^o_i|,       */
+/* collects inside S; each of `spp` samples moves the origin uniformly on a   */
+/* disk of area A_S / M = 4 pi R^2 / M tangent to S at O + R p^o_i, and the   */
+/* texel is the mean of the samples. The scene here is an emission-absorption */
+/* volume of Gaussian blobs (density kappa_b exp(-|x - mu_b|^2 / (2 s_b^2)),  */
+/* emitted radiance per unit length = density times the blob's colour) in    */
+/* front of a background that depends on the direction only. Each sample     */
+/* integrates, from the origin (t = 0) to the far intersection with S, the    */
+/* emission-absorption equation by the midpoint rule with `steps` steps of    */
+/* constant density and emission: L += T (1 - exp(-sigma dt)) / sigma * q,    */
+/* T *= exp(-sigma dt); the background is seen through the final T.           */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t B, C;              /* blobs; channels 3 (RGB) or 4 (RGB + opacity 1 - T) */
+    uint32_t spp, steps;        /* samples per texel; midpoint steps per sample */
+    uint32_t jitter;            /* 1: origins jittered on the disk; 0: at O + R p^o_i */
+    uint32_t pad_;
+    uint64_t seed;              /* counter-based generator (SplitMix64) seed */
+    double R, O[3];
+    const double *mu;           /* [B][3] blob centres */
+    const double *width;        /* [B] s_b > 0 */
+    const double *dens;         /* [B] kappa_b >= 0 (per unit length) */
+    const double *emit;         /* [B][3] emitted colour */
+    double bg0[3], bg1[3];      /* background bg0 + bg1 (1 + d_z) / 2 */
+} lfo_volume;
+
+/* Uniform in [0, 1) on a 2^-24 grid: the top 24 bits of SplitMix64(seed, ctr). */
+static double lfo_u24(uint64_t seed, uint64_t ctr)
+{
+    return ldexp((double)(lfo_splitmix64(seed, ctr) >> 40), -24);
+}
+
+/* Unit direction of the chord from p (origin point) to q (direction point);
+   -p if the two coincide (same convention as the lobe field). */
+static void lfo_chord_dir(const double p[3], const double q[3], double d[3])
+{
+    double v[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
+    double l = sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+    if (l < 1e-12) { d[0] = -p[0]; d[1] = -p[1]; d[2] = -p[2]; return; }
+    d[0] = v[0] / l; d[1] = v[1] / l; d[2] = v[2] / l;
+}
+
+/* Origin of sample s of texel (i, j): O + R p + r (cos a e_phi + sin a e_theta),
+   r = (2R / sqrt(M)) sqrt(u1), a = 2 pi u2, with e_phi, e_theta the unit
+   tangents of the sphere at p along azimuth and polar angle. */
+void lfo_volume_origin(const lfo_volume *V, uint32_t M, uint32_t N, const double p[3],
+                       uint32_t i, uint32_t j, uint32_t s, double o[3])
+{
+    for (int k = 0; k < 3; ++k) o[k] = V->O[k] + V->R * p[k];
+    if (!V->jitter) return;
+    uint64_t ctr = 2ull * (((uint64_t)i * N + j) * V->spp + s);
+    double u1 = lfo_u24(V->seed, ctr), u2 = lfo_u24(V->seed, ctr + 1);
+    double rho = sqrt(p[0] * p[0] + p[1] * p[1]);
+    double ephi[3] = {1.0, 0.0, 0.0}, eth[3] = {0.0, 1.0, 0.0};
+    if (rho > 0.0) {
+        ephi[0] = -p[1] / rho; ephi[1] = p[0] / rho; ephi[2] = 0.0;
+        eth[0] = p[0] * p[2] / rho; eth[1] = p[1] * p[2] / rho; eth[2] = -rho;
+    }
+    double r = 2.0 * V->R / sqrt((double)M) * sqrt(u1), a = 2.0 * LFO_PI * u2;
+    for (int k = 0; k < 3; ++k) o[k] += r * (cos(a) * ephi[k] + sin(a) * eth[k]);
+}
+
+/* Far end of the segment inside S: max(0, -b + sqrt(b^2 - c)), 0 if the line misses. */
+double lfo_volume_tend(const lfo_volume *V, const double o[3], const double d[3])
+{
+    double f[3] = {o[0] - V->O[0], o[1] - V->O[1], o[2] - V->O[2]};
+    double b = (f[0] * d[0] + f[1] * d[1]) + f[2] * d[2];
+    double c = ((f[0] * f[0] + f[1] * f[1]) + f[2] * f[2]) - V->R * V->R;
+    double disc = b * b - c;
+    if (disc <= 0.0) return 0.0;
+    double t = -b + sqrt(disc);
+    return t > 0.0 ? t : 0.0;
+}
+
+/* One ray: radiance rgb[3] (background included) and final transmittance. */
+void lfo_volume_ray(const lfo_volume *V, const double o[3], const double d[3], double rgb[3],
+                    double *T_out)
+{
+    double t_end = lfo_volume_tend(V, o, d);
+    double dt = t_end / (double)V->steps;
+    double T = 1.0, L[3] = {0.0, 0.0, 0.0};
+    for (uint32_t k = 0; k < V->steps && dt > 0.0; ++k) {
+        double t = ((double)k + 0.5) * dt;
+        double x[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+        double sigma = 0.0, q[3] = {0.0, 0.0, 0.0};
+        for (uint32_t b = 0; b < V->B; ++b) {
+            const double *m = V->mu + 3 * b;
+            double r2 = ((x[0] - m[0]) * (x[0] - m[0]) + (x[1] - m[1]) * (x[1] - m[1])) +
+                        (x[2] - m[2]) * (x[2] - m[2]);
+            double g = V->dens[b] * exp(-r2 / (2.0 * V->width[b] * V->width[b]));
+            sigma += g;
+            for (int c = 0; c < 3; ++c) q[c] += g * V->emit[3 * b + c];
+        }
+        if (sigma > 0.0) {
+            double phi = -expm1(-sigma * dt) / sigma;     /* integral of exp(-sigma t) over the step */
+            for (int c = 0; c < 3; ++c) L[c] += T * phi * q[c];
+            T *= exp(-sigma * dt);
+        }
+    }
+    double w = 0.5 * (1.0 + d[2]);
+    for (int c = 0; c < 3; ++c) rgb[c] = L[c] + T * (V->bg0[c] + V->bg1[c] * w);
+    *T_out = T;
+}
+
+/* Texel (i, j): mean over the samples; channel 3 (if C = 4) is the mean opacity. */
+void lfo_volume_texel(const lfo_volume *V, const double *Po, const double *Pd, uint32_t M,
+                      uint32_t N, uint32_t i, uint32_t j, double *out /* [C] */)
+{
+    const double *p = Po + 3ull * i, *q = Pd + 3ull * j;
+    double d[3], acc[4] = {0.0, 0.0, 0.0, 0.0};
+    lfo_chord_dir(p, q, d);
+    for (uint32_t s = 0; s < V->spp; ++s) {
+        double o[3], rgb[3], T;
+        lfo_volume_origin(V, M, N, p, i, j, s, o);
+        lfo_volume_ray(V, o, d, rgb, &T);
+        for (int c = 0; c < 3; ++c) acc[c] += rgb[c];
+        acc[3] += 1.0 - T;
+    }
+    for (uint32_t c = 0; c < V->C; ++c) out[c] = acc[c] / (double)V->spp;
+}
+
+/* FP32 table rows [i0, i1) of the volume scene (FP64 evaluation, rounded once). */
+void lfo_volume_table_rows(const lfo_volume *V, const double *Po, const double *Pd, uint32_t M,
+                           uint32_t N, uint32_t i0, uint32_t i1, float *out /* [(i1-i0)][N][C] */)
+{
+    double v[4];
+    for (uint32_t i = i0; i < i1; ++i)
+        for (uint32_t j = 0; j < N; ++j) {
+            lfo_volume_texel(V, Po, Pd, M, N, i, j, v);
+            for (uint32_t c = 0; c < V->C; ++c)
+                out[(((size_t)(i - i0)) * N + j) * V->C + c] = (float)v[c];
+        }
 }
