@@ -186,6 +186,62 @@ lf_status lf_fill_lobe_table(uint32_t M, uint32_t N, uint32_t C, uint32_t L,
                              const double *kd, const double *col, uint64_t noise_seed,
                              float *out_dev, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Light-field precompute (Section 3): fill L^(i,j) by tracing every ray
+ *   r_k = (O + R p^o_i) + t d_ij,  d_ij = (p^d_j - p^o_i) / |p^d_j - p^o_i|
+ * (-p^o_i if the two points coincide) through an analytic scene inside S, with
+ * the origin of each of `spp` samples jittered uniformly on the disk of area
+ * A_S / M = 4 pi R^2 / M tangent to S at O + R p^o_i; the texel is the mean of
+ * the samples. The scene is an emission-absorption volume of Gaussian blobs
+ * (a stand-in for the paper's path-traced CT data, which is not available):
+ *   density  sigma(x) = sum_b kappa_b exp(-|x - mu_b|^2 / (2 s_b^2)),
+ *   emission q(x)     = sum_b kappa_b exp(...) emit_b        (per unit length),
+ * integrated from the origin (t = 0) to the far intersection of the line with
+ * S by the midpoint rule with `steps` steps of constant sigma and q:
+ *   L += T (1 - exp(-sigma dt)) / sigma * q,   T *= exp(-sigma dt),
+ * plus T times the background bg0 + bg1 (1 + d_z) / 2 of the ray's direction.
+ * Channel 3 (channels = 4) holds the mean opacity 1 - T.
+ * Jitter of sample s of texel (i, j): u1, u2 = the top 24 bits of
+ * SplitMix64(seed, 2 ((i N + j) spp + s)) and of the next counter, times 2^-24;
+ * offset = (2R / sqrt(M)) sqrt(u1) (cos(2 pi u2) e_phi + sin(2 pi u2) e_theta)
+ * with e_phi = (-p_y, p_x, 0) / rho, e_theta = (p_x p_z, p_y p_z, -rho^2) / rho,
+ * rho = sqrt(p_x^2 + p_y^2). SplitMix64(seed, c): z = seed + (c + 1) *
+ * 0x9e3779b97f4a7c15, then the published SplitMix64 finaliser.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    float center[3];     /* mu_b */
+    float width;         /* s_b > 0 */
+    float density;       /* kappa_b >= 0, per unit length */
+    float emit[3];       /* emitted colour per unit density (RGB) */
+} lf_blob;               /* 32 bytes */
+
+#define LF_PRECOMPUTE_MAX_BLOBS 16u
+
+typedef struct {
+    double radius;             /* R > 0 */
+    double center[3];          /* O */
+    uint32_t n_origins;        /* M, 1 .. 2^24 */
+    uint32_t n_directions;     /* N, 1 .. 2^24 */
+    uint32_t channels;         /* 3 (RGB) or 4 (RGB + opacity) */
+    uint32_t rows;             /* origin rows filled, 1 .. M: rows [0, rows), e.g. M/2 for an
+                                  upper-hemisphere table (z_i > 0 exactly for i < M/2) */
+    uint32_t spp;              /* jittered samples per texel, 1 .. 1024 */
+    uint32_t steps;            /* midpoint steps per sample, 1 .. 4096 */
+    uint32_t jitter;           /* 1: jitter the origins; 0: every sample starts at O + R p^o_i */
+    uint32_t n_blobs;          /* 0 .. LF_PRECOMPUTE_MAX_BLOBS */
+    uint64_t seed;             /* generator seed of the jitter */
+    float bg0[3], bg1[3];      /* background */
+} lf_precompute_desc;          /* 96 bytes */
+
+/* Fill out_dev [rows][N][channels] FP32 (device, caller-owned, row-major,
+ * j fastest) with the precomputed light field of the scene `blobs_host`
+ * (n_blobs host structs, read during the call). FP32 arithmetic; the library
+ * allocates and frees a (M + N) x 32-byte point scratch in stream order.
+ * Errors: LF_ERR_INVALID_ARG (NULL, ranges, non-finite or non-positive sizes),
+ * LF_ERR_OUT_OF_MEMORY, LF_ERR_CUDA. Asynchronous on `stream`. */
+lf_status lf_precompute_table(const lf_precompute_desc *desc, const lf_blob *blobs_host,
+                              float *out_dev, void *stream);
+
 /* Largest M + N that lf_render_noalloc accepts. */
 #define LF_NOALLOC_MAX_POINTS 278528u
 
@@ -221,7 +277,7 @@ int lf_device_sm_count(void);
 const char *lf_version(void);
 
 /* sizeof of the ABI structures as compiled into the library, for bindings to
- * check their layouts: which = 0 lf_table_desc, 1 lf_view, 2 lf_launch;
+ * check their layouts: which = 0 lf_table_desc, 1 lf_view, 2 lf_launch, 3 lf_precompute_desc, 4 lf_blob;
  * 0 for any other value. */
 size_t lf_struct_size(int which);
 

@@ -148,8 +148,8 @@ class Volume:
     width: np.ndarray   # [B]
     dens: np.ndarray    # [B]
     emit: np.ndarray    # [B,3]
-    bg0: Tuple[float, float, float] = (0.02, 0.02, 0.03)
-    bg1: Tuple[float, float, float] = (0.10, 0.12, 0.20)
+    bg0: Tuple[float, float, float] = (0.125, 0.125, 0.1875)
+    bg1: Tuple[float, float, float] = (0.25, 0.375, 0.5)
     spp: int = 4
     steps: int = 64
     jitter: int = 1
@@ -174,9 +174,11 @@ def draw_volume(seed: int, B: int = 8, R: float = 1.0, O=(0.0, 0.0, 0.0), spp: i
     width = rng.uniform(0.08, 0.25, B) * R
     dens = rng.uniform(2.0, 12.0, B) / R
     emit = rng.uniform(0.0, 1.0, (B, 3))
-    return Volume(np.ascontiguousarray(mu), np.ascontiguousarray(width), np.ascontiguousarray(dens),
-                  np.ascontiguousarray(emit), spp=spp, steps=steps, jitter=jitter, seed=int(seed),
-                  R=float(R), O=tuple(float(x) for x in O))
+
+    def f32(a):     # parameters exactly representable in FP32 (the library's input type)
+        return np.ascontiguousarray(np.asarray(a, np.float32).astype(np.float64))
+    return Volume(f32(mu), f32(width), f32(dens), f32(emit), spp=spp, steps=steps, jitter=jitter,
+                  seed=int(seed), R=float(R), O=tuple(float(x) for x in O))
 
 
 # --------------------------------------------------------------------------

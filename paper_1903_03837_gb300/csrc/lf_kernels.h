@@ -61,6 +61,31 @@ cudaError_t launch_fill_lobe(const LobeParams &P, const float4 *po_hi, const flo
                              const float4 *pd_hi, const float4 *pd_lo, uint32_t M, uint32_t N,
                              float *out, cudaStream_t st);
 
+// SplitMix64 (Steele, Lea, Flood 2014): output number ctr+1 of the stream
+// seeded with `seed` (the counter-based generator of the synthetic inputs).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t ctr)
+{
+    uint64_t z = seed + (ctr + 1ull) * 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// lf_precompute.cu: the light-field precompute of Section 3 (volume scene).
+constexpr int kMaxBlobs = 16;
+struct PrecomputeParams {
+    const float4 *po_hi, *po_lo, *pd_hi, *pd_lo;   // SF points (hi + lo parts)
+    float *out;                                     // [rows][N][C]
+    float Ox, Oy, Oz, R;                            // sphere S
+    float disk_r;                                   // 2R / sqrt(M): disk of area 4 pi R^2 / M
+    uint32_t N, C, rows, spp, steps, jitter, nb;
+    uint64_t seed;
+    float bg0[3], bg1[3];
+    float4 blob_pos[kMaxBlobs];    // centre xyz, log2(kappa_b) (-inf for kappa_b = 0)
+    float4 blob_col[kMaxBlobs];    // emit rgb, a_b = sqrt(log2(e) / 2) / s_b
+};
+cudaError_t launch_precompute(const PrecomputeParams &p, cudaStream_t st);
+
 // Fills the conservative-miss constants of a view for sphere (R, O) (lf_abi.cu).
 void fill_view_miss_consts(ViewK &k, double R, const double O[3]);
 

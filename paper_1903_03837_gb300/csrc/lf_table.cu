@@ -129,16 +129,6 @@ cudaError_t launch_quantize(const float *src, uint32_t M, uint32_t N, uint32_t C
     return cudaGetLastError();
 }
 
-// SplitMix64 (Steele, Lea, Flood 2014): output number ctr+1 of the stream
-// seeded with `seed`.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t ctr)
-{
-    uint64_t z = seed + (ctr + 1ull) * 0x9e3779b97f4a7c15ull;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-
 __device__ __forceinline__ double dot3(const double a[3], const double b[3])
 {
     return __dadd_rn(__dadd_rn(__dmul_rn(a[0], b[0]), __dmul_rn(a[1], b[1])), __dmul_rn(a[2], b[2]));

@@ -49,6 +49,21 @@ class lf_launch(C.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class lf_blob(C.Structure):
+    _fields_ = [("center", C.c_float * 3), ("width", C.c_float), ("density", C.c_float),
+                ("emit", C.c_float * 3)]
+
+
+class lf_precompute_desc(C.Structure):
+    _fields_ = [("radius", C.c_double), ("center", C.c_double * 3), ("n_origins", C.c_uint32),
+                ("n_directions", C.c_uint32), ("channels", C.c_uint32), ("rows", C.c_uint32),
+                ("spp", C.c_uint32), ("steps", C.c_uint32), ("jitter", C.c_uint32),
+                ("n_blobs", C.c_uint32), ("seed", C.c_uint64), ("bg0", C.c_float * 3),
+                ("bg1", C.c_float * 3)]
+
+
+LF_PRECOMPUTE_MAX_BLOBS = 16
+
 _lib = None
 _lock = threading.Lock()
 
@@ -81,12 +96,13 @@ def lib():
                 "lf_struct_size": (C.c_size_t, [C.c_int]),
                 "lf_render_noalloc": (st, [C.POINTER(lf_table_desc), vp, vp, C.POINTER(lf_view), u32,
                                            C.POINTER(lf_launch), vp, vp, vp]),
+                "lf_precompute_table": (st, [C.POINTER(lf_precompute_desc), C.POINTER(lf_blob), vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
                 f.restype = res
                 f.argtypes = args
-            for k, s in enumerate((lf_table_desc, lf_view, lf_launch)):
+            for k, s in enumerate((lf_table_desc, lf_view, lf_launch, lf_precompute_desc, lf_blob)):
                 if L.lf_struct_size(k) != C.sizeof(s):
                     raise RuntimeError(f"ABI mismatch: {s.__name__} is {C.sizeof(s)} bytes here, "
                                        f"{L.lf_struct_size(k)} in the library")
@@ -186,6 +202,11 @@ def lf_render_noalloc(desc: lf_table_desc, radiance_ptr: int, scales_ptr: Option
                                    views, n_views, C.byref(launch) if launch is not None else None,
                                    C.c_void_p(out_ptr), C.c_void_p(idx_ptr or None),
                                    C.c_void_p(stream or None)))
+
+
+def lf_precompute_table(desc: lf_precompute_desc, blobs, out_ptr: int, stream: int = 0):
+    """Light-field precompute of a volume scene into a device FP32 table (Section 3)."""
+    _check(lib().lf_precompute_table(C.byref(desc), blobs, C.c_void_p(out_ptr), C.c_void_p(stream or None)))
 
 
 def lf_device_sm_count() -> int:

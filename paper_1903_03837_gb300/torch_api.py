@@ -158,6 +158,38 @@ def fill_lobe_table(lobes, M: int, N: int, out: Optional[torch.Tensor] = None) -
     return out
 
 
+def precompute_table(volume, M: int, N: int, C: int = 4, rows: Optional[int] = None,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """FP32 [rows, N, C] light field of an emission-absorption volume scene
+    (Section 3: rays r_k with jittered origins; `volume` as lf_inputs.Volume:
+    mu, width, dens, emit, bg0, bg1, spp, steps, jitter, seed, R, O)."""
+    rows = M if rows is None else int(rows)
+    if out is None:
+        out = torch.empty((rows, N, C), dtype=torch.float32, device="cuda")
+    _need_cuda(out, "out")
+    if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != rows * N * C:
+        raise ValueError("out must be a contiguous float32 tensor of rows * N * C elements")
+    B = len(volume.width)
+    if B > lp.LF_PRECOMPUTE_MAX_BLOBS:
+        raise ValueError(f"at most {lp.LF_PRECOMPUTE_MAX_BLOBS} blobs")
+    blobs = (lp.lf_blob * max(B, 1))()
+    for b in range(B):
+        blobs[b].center[:] = [float(x) for x in volume.mu[b]]
+        blobs[b].width = float(volume.width[b])
+        blobs[b].density = float(volume.dens[b])
+        blobs[b].emit[:] = [float(x) for x in volume.emit[b]]
+    d = lp.lf_precompute_desc()
+    d.radius = float(volume.R)
+    d.center[:] = [float(x) for x in volume.O]
+    d.n_origins, d.n_directions, d.channels, d.rows = M, N, C, rows
+    d.spp, d.steps, d.jitter, d.n_blobs = int(volume.spp), int(volume.steps), int(volume.jitter), B
+    d.seed = int(volume.seed) & (2**64 - 1)
+    d.bg0[:] = [float(x) for x in volume.bg0]
+    d.bg1[:] = [float(x) for x in volume.bg1]
+    lp.lf_precompute_table(d, blobs, out.data_ptr(), _stream())
+    return out
+
+
 def quantize_table(T: torch.Tensor, dtype: str) -> Tuple[torch.Tensor, torch.Tensor]:
     """Per-row FP16 / E4M3 codes [M,N,4] (int16 holding binary16 bits, or uint8)
     and scales [M] of an FP32 [M,N,C] table."""

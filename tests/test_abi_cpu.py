@@ -38,6 +38,8 @@ def test_struct_layouts_match():
     assert L.lf_struct_size(0) == C.sizeof(lp.lf_table_desc) == 56
     assert L.lf_struct_size(1) == C.sizeof(lp.lf_view) == 72
     assert L.lf_struct_size(2) == C.sizeof(lp.lf_launch) == 24
+    assert L.lf_struct_size(3) == C.sizeof(lp.lf_precompute_desc) == 96
+    assert L.lf_struct_size(4) == C.sizeof(lp.lf_blob) == 32
     assert L.lf_struct_size(7) == 0
 
 
@@ -116,3 +118,57 @@ def test_error_message_is_thread_local():
     t.start()
     t.join()
     assert "channels" in mine and seen == [""]
+
+
+def _pdesc(**kw):
+    d = lp.lf_precompute_desc()
+    d.radius = kw.get("radius", 1.0)
+    d.center[:] = kw.get("center", [0.0, 0.0, 0.0])
+    d.n_origins = kw.get("M", 64)
+    d.n_directions = kw.get("N", 32)
+    d.channels = kw.get("C", 4)
+    d.rows = kw.get("rows", d.n_origins)
+    d.spp = kw.get("spp", 4)
+    d.steps = kw.get("steps", 16)
+    d.jitter = kw.get("jitter", 1)
+    d.n_blobs = kw.get("nb", 1)
+    d.seed = 1
+    d.bg0[:] = kw.get("bg0", [0.0, 0.0, 0.0])
+    d.bg1[:] = [0.0, 0.0, 0.0]
+    return d
+
+
+def _blobs(width=0.2, density=3.0, n=1):
+    b = (lp.lf_blob * max(n, 1))()
+    for k in range(n):
+        b[k].center[:] = [0.0, 0.0, 0.0]
+        b[k].width = width
+        b[k].density = density
+        b[k].emit[:] = [1.0, 0.5, 0.25]
+    return b
+
+
+@pytest.mark.parametrize("kw,blob", [
+    (dict(M=0), {}), (dict(N=1 << 25), {}), (dict(radius=0.0), {}), (dict(radius=float("nan")), {}),
+    (dict(C=2), {}), (dict(rows=0), {}), (dict(rows=65), {}), (dict(spp=0), {}), (dict(spp=2000), {}),
+    (dict(steps=0), {}), (dict(steps=5000), {}), (dict(jitter=2), {}), (dict(nb=17), {}),
+    (dict(bg0=[float("inf"), 0.0, 0.0]), {}), ({}, dict(width=0.0)), ({}, dict(width=-1.0)),
+    ({}, dict(density=-0.5)), ({}, dict(density=float("nan"))),
+])
+def test_precompute_rejects_bad_arguments(kw, blob):
+    # validation happens before any CUDA call; the fake output pointer is never touched
+    L = lp.lib()
+    d = _pdesc(**kw)
+    st = L.lf_precompute_table(C.byref(d), _blobs(n=max(1, d.n_blobs), **blob), C.c_void_p(4096), None)
+    assert st == lp.LF_ERR_INVALID_ARG, (kw, blob, lp.lf_last_error())
+    assert lp.lf_last_error()
+
+
+def test_precompute_null_and_misaligned_arguments():
+    L = lp.lib()
+    d = _pdesc()
+    assert L.lf_precompute_table(None, _blobs(), C.c_void_p(4096), None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_precompute_table(C.byref(d), _blobs(), None, None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_precompute_table(C.byref(d), None, C.c_void_p(4096), None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_precompute_table(C.byref(d), _blobs(), C.c_void_p(4100), None) == lp.LF_ERR_INVALID_ARG
+    assert "aligned" in lp.lf_last_error()
