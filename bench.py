@@ -256,6 +256,35 @@ def run_ours(args, rank: int, world: int):
         psnr_vs_f32[dt] = 10 * math.log10(float(r.max()) ** 2 / mse) if mse > 0 else float("inf")
     gpu_images = {dt: tables[dt].render(frame_views[f0])[0] for dt in ("f32", "f16", "e4m3")}
 
+    # Neighbour count (Section 2: nearest sampling, five, "up to nine"): the same
+    # frames and launch shape on the headline table with K = 1 and K = 9, and the
+    # FP32-table image of each K for the quality comparison of the CPU leg.
+    neighbours = {5: {"grays_s": world * args.steps * rays / (total_ms * 1e-3) / 1e9,
+                      "ms_per_step": total_ms / args.steps}}
+    k_images = {5: gpu_images["f32"]}
+    if not args.no_variants and args.workload == "large":
+        for K in (1, 9):
+            c, sc = codes[args.dtype] if args.dtype != "f32" else (T32, None)
+            lfk = api.LightField(c, args.dtype, sc, borrow=True, k_nearest=K)
+            lfk.set_launch(**launch)
+            for k in range(3):
+                lfk.render(frame_views[my_frames[k]], out=outs[k % 2])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.steps):
+                lfk.render(frame_views[my_frames[args.warmup + k]], out=outs[k % 2])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            neighbours[K] = {"grays_s": world * rays / (ms * 1e-3) / 1e9, "ms_per_step": ms}
+            lfk.close()
+            lf32 = api.LightField(T32, "f32", borrow=True, k_nearest=K)
+            lf32.set_launch(**launch)
+            k_images[K] = lf32.render(frame_views[f0])[0]
+            torch.cuda.synchronize()
+            lf32.close()
+
     # End to end through the public API: the host views go in with each call and
     # every frame's image is read back to pinned host memory. Double-buffered:
     # frame k+1 renders on the compute stream while frame k copies on a second one.
@@ -336,6 +365,7 @@ def run_ours(args, rank: int, world: int):
         "gpu_launches": args.steps,
         "variants": variants,
         "psnr_vs_f32_table_db": psnr_vs_f32,
+        "neighbours": {str(k): v for k, v in sorted(neighbours.items())},
     }
     if not args.no_variants:
         for t in tables.values():
@@ -351,8 +381,10 @@ def run_ours(args, rank: int, world: int):
         line["precompute"] = run_precompute(args)
         tables = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "large":
-        line["cpu_baseline"], psnr64 = cpu_baseline(cfg, frame_views[f0], gpu_images, args)
+        line["cpu_baseline"], psnr64, psnr_k = cpu_baseline(cfg, frame_views[f0], gpu_images, args, k_images)
         line["psnr_vs_fp64_db"] = psnr64
+        for k, v in psnr_k.items():
+            line["neighbours"][str(k)]["psnr_vs_continuous_field_db"] = v
     for t in tables.values():
         t.close()
     return line
@@ -546,9 +578,11 @@ def run_paper_shape(args):
                              "render, resolution not stated); other hardware, context only"}
 
 
-def cpu_baseline(cfg, views, gpu_images, args):
+def cpu_baseline(cfg, views, gpu_images, args, k_images=None):
     """The CPU oracle (brute-force K-NN, FP64) on a bounded random sample of the
-    frame's pixels; also the FP64 reference of those pixels for PSNR."""
+    frame's pixels; also the FP64 reference of those pixels for PSNR, and the
+    continuous lobe field along each sampled pixel's ray, the reference for the
+    images of each neighbour count (FP32 table, so only interpolation differs)."""
     import oracle
     cores = host_cores()
     sc = oracle.Scene(cfg.M, cfg.N, 4, "lobe", lobes=cfg.lobes())
@@ -569,11 +603,18 @@ def cpu_baseline(cfg, views, gpu_images, args):
     for k, img in gpu_images.items():
         g = img.cpu().numpy().astype(np.float64)[offs]
         psnr[k] = oracle.psnr(ref, g, hit)
+    psnr_k = {}
+    if k_images:
+        cont, chit = oracle.lobe_reference_pixels(cfg.lobes(), views, pix, threads=cores)
+        cont[chit] += 0.005          # the mean of the texels' U(0, 0.01) noise
+        for k, img in k_images.items():
+            g = img.cpu().numpy().astype(np.float64)[offs]
+            psnr_k[k] = oracle.psnr(cont, g, chit & hit)
     base = {"value": n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n:,} random pixels of orbit frame 0 ({hits:,} hits), brute-force FP64 K-NN "
                       f"over all {cfg.M:,}+{cfg.N:,} SF points, texels from the FP64 lobe field; "
                       f"{dt:.1f} s on {cores} threads"}
-    return base, psnr
+    return base, psnr, psnr_k
 
 
 # ---------------------------------------------------------------------------

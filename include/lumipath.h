@@ -68,7 +68,8 @@ typedef struct lf_table_desc {
     uint32_t channels;         /* C in {3, 4} */
     int32_t dtype;             /* lf_dtype */
     uint32_t flags;            /* LF_TABLE_* */
-    uint32_t k_nearest;        /* neighbours per hit: 5 (0 means 5), or 1 for nearest sampling */
+    uint32_t k_nearest;        /* neighbours per hit: 5 (0 means 5), 1 for nearest sampling, or 9
+                                  (the "up to nine" of Section 2: 9 x 9 = 81 taps per ray) */
 } lf_table_desc;
 
 /* A pinhole camera. Pixel (x, y) of a W x H image looks along
@@ -119,7 +120,7 @@ typedef struct lf_table lf_table;
  * Also builds the SF point caches of both sets on `stream`.
  * Errors: LF_ERR_INVALID_ARG (null desc/out/radiance, bad sizes, R <= 0 or
  *   non-finite, missing scales, unsupported channel count), LF_ERR_UNSUPPORTED
- *   (k_nearest other than 0, 1 or 5),
+ *   (k_nearest other than 0, 1, 5 or 9),
  *   LF_ERR_OUT_OF_MEMORY, LF_ERR_CUDA. On error *out is NULL. */
 lf_status lf_create_table(const lf_table_desc *desc, const void *radiance_dev,
                           const float *row_scales_dev, void *stream, lf_table **out);

@@ -99,6 +99,8 @@ def lib():
                 "lfo_render_pixels": (i64, [vp, vp, vp, vp, i64, vp, vp]),
                 "lfo_render_backward_pixels": (None, [vp, vp, vp, vp, i64, vp, vp]),
                 "lfo_trace_pixel": (C.c_int, [dbl, vp, vp, u32, u32, u32, u32, vp, vp, vp, vp, vp]),
+                "lfo_lobe_continuous": (None, [vp, vp, vp, vp]),
+                "lfo_lobe_reference_pixels": (i64, [vp, dbl, vp, vp, vp, vp, i64, vp, vp]),
                 "lfo_volume_origin": (None, [vp, u32, u32, vp, u32, u32, u32, vp]),
                 "lfo_volume_tend": (dbl, [vp, vp, vp]),
                 "lfo_volume_ray": (None, [vp, vp, vp, vp, vp]),
@@ -271,6 +273,37 @@ def lobe_texel(lobes, M: int, N: int, i: int, j: int) -> np.ndarray:
     out = np.zeros(16)
     lib().lfo_lobe_texel(C.byref(h.s), _p(sf_points(M)), _p(sf_points(N)), i, j, _p(out))
     return out[:lobes.C].copy()
+
+
+def lobe_continuous(lobes, q, d) -> np.ndarray:
+    """The lobe field at origin q (unit) and direction d (unit), without noise."""
+    h = _LobesHold(lobes)
+    out = np.zeros(16)
+    lib().lfo_lobe_continuous(C.byref(h.s), _p(np.ascontiguousarray(q, np.float64)),
+                              _p(np.ascontiguousarray(d, np.float64)), _p(out))
+    return out[:lobes.C].copy()
+
+
+def lobe_reference_pixels(lobes, views, pix: np.ndarray, R: float = 1.0, O=(0.0, 0.0, 0.0),
+                          threads: Optional[int] = None):
+    """Continuous lobe field along each pixel's ray (at the normalised front hit,
+    in the chord direction to the back hit): (out [np,C] FP64, hit [np] bool)."""
+    h = _LobesHold(lobes)
+    vf, wh = _views_arrays(views)
+    pix = np.ascontiguousarray(pix, np.uint32)
+    out = np.zeros((len(pix), lobes.C))
+    hit = np.zeros(len(pix), np.uint8)
+    Od = (C.c_double * 3)(*[float(o) for o in O])
+    chunks = np.array_split(np.arange(len(pix)), _threads(threads) * 4)
+
+    def work(ch):
+        if len(ch):
+            a = int(ch[0])
+            lib().lfo_lobe_reference_pixels(C.byref(h.s), float(R), Od, _p(vf), _p(wh), _p(pix[a:]),
+                                            len(ch), _p(out[a:]), _p(hit[a:]))
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(work, chunks))
+    return out, hit.astype(bool)
 
 
 def lobe_table(lobes, M: int, N: int, rows: Optional[Sequence[int]] = None,

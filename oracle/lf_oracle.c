@@ -333,6 +333,54 @@ void lfo_lobe_table_rows(const lfo_lobes *lb, const double *Po, const double *Pd
         }
 }
 
+static void lfo_chord_dir(const double p[3], const double q[3], double d[3]);
+
+/* The lobe field as a continuous function of an origin q on the unit sphere
+   and a unit direction d: the texel formula with p^o_i -> q and d_ij -> d,
+   without the per-texel noise. The table samples this function at the SF
+   points; rendering interpolates it, so it is the reference of image quality
+   for a given neighbour count. */
+void lfo_lobe_continuous(const lfo_lobes *lb, const double q[3], const double d[3],
+                         double *out /* [C] */)
+{
+    for (uint32_t c = 0; c < lb->C; ++c) out[c] = 0.0;
+    for (uint32_t k = 0; k < lb->L; ++k) {
+        const double *a = lb->ap + 3 * k, *b = lb->ad + 3 * k;
+        double cp = (q[0] * a[0] + q[1] * a[1]) + q[2] * a[2];
+        double cd = (d[0] * b[0] + d[1] * b[1]) + d[2] * b[2];
+        double g = exp(lb->kp[k] * (cp - 1.0)) * exp(lb->kd[k] * (cd - 1.0));
+        for (uint32_t c = 0; c < lb->C; ++c) out[c] += lb->col[k * lb->C + c] * g;
+    }
+}
+
+/* Reference pixels: the continuous lobe field at the pixel's normalised front
+   hit and the unit chord direction from the front to the back hit (the ray's
+   own direction inside S); hit[p] = 0 and out 0 for a miss. */
+int64_t lfo_lobe_reference_pixels(const lfo_lobes *lb, double R, const double O[3], const float *views,
+                                  const uint32_t *wh, const uint32_t *pix, int64_t np, double *out,
+                                  uint8_t *hit)
+{
+    int64_t hits = 0;
+    float O32[3] = {(float)O[0], (float)O[1], (float)O[2]};
+    for (int64_t p = 0; p < np; ++p) {
+        uint32_t v = pix[3 * p], x = pix[3 * p + 1], y = pix[3 * p + 2];
+        const float *vw = views + 14 * v;
+        float d[3], ho[3], hd[3];
+        for (uint32_t c = 0; c < lb->C; ++c) out[p * lb->C + c] = 0.0;
+        hit[p] = 0;
+        lfo_camera_ray(vw, wh[2 * v], wh[2 * v + 1], x, y, d);
+        if (!lfo_intersect((float)R, O32, vw, d, ho, hd)) continue;
+        double qo[3], qd[3], u[3];
+        lfo_normalize_hit(ho, O, qo);
+        lfo_normalize_hit(hd, O, qd);
+        lfo_chord_dir(qo, qd, u);
+        lfo_lobe_continuous(lb, qo, u, out + p * lb->C);
+        hit[p] = 1;
+        ++hits;
+    }
+    return hits;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Rendering (Section 2): per pixel, ray -> hits -> K-NN of each hit ->       */
 /* tent weights -> sum_ab W_ab * L^(i_a, j_b).                                */

@@ -133,7 +133,8 @@ lf_status run_chunk(const lf_table *t, const lfk::RenderParamsBase &base, const 
     unsigned grid = (unsigned)tiles;
     if (L.persistent) {
         int per_sm = L.ctas_per_sm ? (int)L.ctas_per_sm
-                                   : lfk::render_occupancy(t->texel_kind, bwd, MAXV != lfk::kSmallViews, block);
+                                   : lfk::render_occupancy(t->texel_kind, bwd, MAXV != lfk::kSmallViews,
+                                                           p.nine != 0, block);
         uint64_t g = (uint64_t)t->sm_count * (uint64_t)per_sm;
         grid = (unsigned)(g < tiles ? g : tiles);
     }
@@ -181,6 +182,7 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
     b.ww_log = (uint32_t)__builtin_ctz(t->launch.warp_w);
     b.rows_valid = t->rows;
     b.nearest_only = t->desc.k_nearest == 1 ? 1u : 0u;
+    b.nine = t->desc.k_nearest == 9 ? 1u : 0u;
     b.rows_stored = (t->desc.flags & LF_TABLE_UPPER_HEMISPHERE) ? t->rows : 0u;
     const bool bwd = grad != nullptr;
     cudaStream_t st = (cudaStream_t)stream;
@@ -268,8 +270,8 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
     if (C != 3 && C != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4 (got %u)", C);
     if (d->dtype != LF_DTYPE_F32 && d->dtype != LF_DTYPE_F16 && d->dtype != LF_DTYPE_E4M3)
         return fail(LF_ERR_INVALID_ARG, "unknown dtype %d", d->dtype);
-    if (d->k_nearest != 0 && d->k_nearest != 1 && d->k_nearest != 5)
-        return fail(LF_ERR_UNSUPPORTED, "k_nearest=%u: 1 or 5 neighbours per hit are built", d->k_nearest);
+    if (d->k_nearest != 0 && d->k_nearest != 1 && d->k_nearest != 5 && d->k_nearest != 9)
+        return fail(LF_ERR_UNSUPPORTED, "k_nearest=%u: 1, 5 or 9 neighbours per hit are built", d->k_nearest);
     if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
         return fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
     const bool upper = (d->flags & LF_TABLE_UPPER_HEMISPHERE) != 0;

@@ -30,7 +30,8 @@ struct RenderParamsBase {
     uint32_t tw_log, th_log, ww_log;   // log2 of tile_w, tile_h, warp_w
     uint32_t rows_stored;              // origin rows present (upper hemisphere), 0: all
     uint32_t rows_valid;               // rows of the table (M or rows_stored)
-    uint32_t nearest_only;             // 1: nearest sampling (K = 1), else 5 neighbours
+    uint32_t nearest_only;             // 1: nearest sampling (K = 1), else 5 or 9 neighbours
+    uint32_t nine;                     // 1: 9 neighbours per hit (81 taps)
 };
 
 template <int MAXV>
@@ -43,7 +44,7 @@ cudaError_t launch_render_small(int kind, bool bwd, const RenderParams<kSmallVie
                                 unsigned block, cudaStream_t st);
 cudaError_t launch_render_large(int kind, bool bwd, const RenderParams<kLargeViews> &p, unsigned grid,
                                 unsigned block, cudaStream_t st);
-int render_occupancy(int kind, bool bwd, bool large, unsigned block);
+int render_occupancy(int kind, bool bwd, bool large, bool nine, unsigned block);
 
 // lf_table.cu
 cudaError_t launch_build_points(uint32_t n, float4 *hi, float4 *lo, cudaStream_t st);

@@ -102,7 +102,7 @@ lf_status launch_views(const lfk::RenderParamsBase &base, const lf_launch &L, in
     unsigned grid = (unsigned)tiles;
     if (L.persistent) {
         int per_sm = L.ctas_per_sm ? (int)L.ctas_per_sm
-                                   : lfk::render_occupancy(kind, false, MAXV != lfk::kSmallViews, block);
+                                   : lfk::render_occupancy(kind, false, MAXV != lfk::kSmallViews, false, block);
         uint64_t g = (uint64_t)sm_count * (uint64_t)per_sm;
         grid = (unsigned)(g < tiles ? g : tiles);
     }
@@ -143,7 +143,7 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
     if (quant && (C != 4 || !row_scales_dev))
         return na_fail(LF_ERR_INVALID_ARG, "F16/E4M3 tables need 4 channels and row scales here");
     if (d->k_nearest != 0 && d->k_nearest != 1 && d->k_nearest != 5)
-        return na_fail(LF_ERR_UNSUPPORTED, "1 or 5 neighbours per hit are built");
+        return na_fail(LF_ERR_UNSUPPORTED, "1 or 5 neighbours per hit here (9: lf_render)");
     if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
         return na_fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
     if ((d->flags & LF_TABLE_UPPER_HEMISPHERE) && M < 2)

@@ -59,15 +59,17 @@ __device__ __forceinline__ void pixel_of(const RenderParamsBase &p, uint32_t tx,
     py = (ty << p.th_log) + ((warp >> wx_log) << (5u - p.ww_log)) + (lane >> p.ww_log);
 }
 
-// Indices and normalised weights of one ray; false for a miss.
+// Indices and normalised weights of one ray (K = 5 or 9 neighbours per hit);
+// false for a miss.
+template <int K>
 __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const ViewK &v, uint32_t px,
-                                            uint32_t py, int32_t io[5], int32_t jd[5], float wo[5],
-                                            float wd[5])
+                                            uint32_t py, int32_t (&io)[K], int32_t (&jd)[K], float (&wo)[K],
+                                            float (&wd)[K])
 {
     // The origin set's indices and weights wait in shared memory (one slot per
-    // thread, no synchronisation) while the direction set is searched: ten
+    // thread, no synchronisation) while the direction set is searched: 2K
     // fewer live registers across the second search.
-    __shared__ int s_stash[10 * kMaxBlock];
+    __shared__ int s_stash[2 * K * kMaxBlock];
     float3 d = camera_dir(v, px, py);
     float3 ho, hd;
     if (!intersect_sphere(p.sphere, v.eye, d, ho, hd)) return false;
@@ -80,15 +82,19 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
         P.n = s ? p.pd.n : p.po.n;
         P.nf = s ? p.pd.nf : p.po.nf;
         P.inv_sigma = s ? p.pd.inv_sigma : p.po.inv_sigma;
-        Top5 r = knn5(P, p.sphere, s ? hd : ho, p.status);
-        float w[5];
+        TopK<K> r;
+        if constexpr (K == 9)
+            r = knn9(P, p.sphere, s ? hd : ho, p.status);
+        else
+            r = knn5(P, p.sphere, s ? hd : ho, p.status);
+        float w[K];
         if (p.nearest_only) {
             // nearest sampling: the nearest point alone (Section 2, Fig. 2)
             if (s == 0 && p.rows_stored && (uint32_t)r.i[0] >= p.rows_stored) return false;
 #pragma unroll
-            for (int m = 0; m < 5; ++m) w[m] = m == 0 ? 1.0f : 0.0f;
+            for (int m = 0; m < K; ++m) w[m] = m == 0 ? 1.0f : 0.0f;
 #pragma unroll
-            for (int m = 1; m < 5; ++m) r.i[m] = -1;
+            for (int m = 1; m < K; ++m) r.i[m] = -1;
         } else if (s == 0 && p.rows_stored) {
             if (!tent_weights_kept(r.d2, r.i, r.cnt, P.inv_sigma, p.rows_stored, w)) return false;
         } else {
@@ -96,22 +102,22 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
         }
         if (s == 0) {
 #pragma unroll
-            for (int m = 0; m < 5; ++m) {
+            for (int m = 0; m < K; ++m) {
                 s_stash[m * kMaxBlock + threadIdx.x] = r.i[m];
-                s_stash[(5 + m) * kMaxBlock + threadIdx.x] = __float_as_int(w[m]);
+                s_stash[(K + m) * kMaxBlock + threadIdx.x] = __float_as_int(w[m]);
             }
         } else {
 #pragma unroll
-            for (int m = 0; m < 5; ++m) {
+            for (int m = 0; m < K; ++m) {
                 jd[m] = r.i[m];
                 wd[m] = w[m];
             }
         }
     }
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
+    for (int m = 0; m < K; ++m) {
         io[m] = s_stash[m * kMaxBlock + threadIdx.x];
-        wo[m] = __int_as_float(s_stash[(5 + m) * kMaxBlock + threadIdx.x]);
+        wo[m] = __int_as_float(s_stash[(K + m) * kMaxBlock + threadIdx.x]);
     }
     return true;
 }
@@ -127,20 +133,21 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
     return *reinterpret_cast<float2 *>(&rd);
 }
 
-template <int DT>
+template <int DT, int K>
 __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const ViewK &v, uint32_t px,
                                            uint32_t py)
 {
-    int32_t io[5], jd[5];
-    float wo[5], wd[5];
+    int32_t io[K], jd[K];
+    float wo[K], wd[K];
     float2 acc_xy = make_float2(0.f, 0.f), acc_zw = make_float2(0.f, 0.f);
     bool hit = !certain_miss(v, px, py) && ray_samples(p, v, px, py, io, jd, wo, wd);
     if (hit) {
-        // All 25 taps in every mode: with nearest sampling the other 24 have
+        // All K x K taps in every mode: with nearest sampling the other 24 have
         // weight 0 and index -1 (row 0, texel 0, an L1 hit), which costs less
-        // than a second copy of the loop.
-#pragma unroll
-        for (int a = 0; a < 5; ++a) {
+        // than a second copy of the loop. The 81 taps of K = 9 keep the outer
+        // loop rolled (instruction-cache footprint).
+#pragma unroll(K == 5 ? 5 : 1)
+        for (int a = 0; a < K; ++a) {
             // a missing or unstored neighbour has weight 0 and reads row 0
             int32_t i = (uint32_t)io[a] < p.rows_valid ? io[a] : 0;
             float s = wo[a];
@@ -148,7 +155,7 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
             size_t row = (size_t)i * p.N;
             float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int b = 0; b < 5; ++b) {
+            for (int b = 0; b < K; ++b) {
                 float4 t = texel<DT>(p.texels, row + (uint32_t)max(jd[b], 0));
                 float2 w2 = make_float2(wd[b], wd[b]);
                 in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
@@ -160,7 +167,7 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
         }
     } else {
 #pragma unroll
-        for (int a = 0; a < 5; ++a) io[a] = jd[a] = -1;
+        for (int a = 0; a < K; ++a) io[a] = jd[a] = -1;
     }
     const float4 acc = make_float4(acc_xy.x, acc_xy.y, acc_zw.x, acc_zw.y);
     uint64_t pix = v.out_offset + (uint64_t)py * v.width + px;
@@ -173,7 +180,14 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
         __stcs(o + 2, acc.z);
     }
     if (p.idx) {
-        if (p.nearest_only) {
+        if constexpr (K == 9) {
+            int2 *q = reinterpret_cast<int2 *>(p.idx + pix * 18);
+#pragma unroll
+            for (int m = 0; m < 9; ++m) {
+                const int e0 = 2 * m, e1 = 2 * m + 1;
+                q[m] = make_int2(e0 < 9 ? io[e0] : jd[e0 - 9], e1 < 9 ? io[e1] : jd[e1 - 9]);
+            }
+        } else if (p.nearest_only) {
             reinterpret_cast<int2 *>(p.idx)[pix] = make_int2(io[0], jd[0]);
         } else {
             int2 *q = reinterpret_cast<int2 *>(p.idx + pix * 10);
@@ -233,16 +247,17 @@ __device__ __forceinline__ void add_to_grad(const RenderParamsBase &p, uint64_t 
     }
 }
 
-// Backward of one ray: grad[i_a][j_b] += W_ab * g for the 25 taps. Lanes that
+// Backward of one ray: grad[i_a][j_b] += W_ab * g for the K x K taps. Lanes that
 // hold the same texel key are summed first (warp aggregation): when every live
 // lane of the warp has the same key, a butterfly over the warp and one atomic;
 // otherwise __match_any_sync groups and a tree sum per group, one atomic per
 // group. The tap loop stays rolled (instruction-cache footprint).
+template <int K>
 __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const ViewK *v, bool active,
                                              uint32_t px, uint32_t py)
 {
-    int32_t io[5], jd[5];
-    float wo[5], wd[5];
+    int32_t io[K], jd[K];
+    float wo[K], wd[K];
     bool hit = false;
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) {
@@ -258,8 +273,8 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
     const unsigned lane = threadIdx.x & 31;
     if (!__any_sync(0xffffffffu, hit)) return;
 #pragma unroll 1
-    for (int t = 0; t < 25; ++t) {
-        const int a = t / 5, b = t - 5 * (t / 5);
+    for (int t = 0; t < K * K; ++t) {
+        const int a = t / K, b = t - K * (t / K);
         bool live = hit && (uint32_t)io[a] < p.rows_valid && jd[b] >= 0;
         uint64_t key = live ? (uint64_t)io[a] * p.N + (uint64_t)jd[b] : 0ull;
         float W = live ? wo[a] * wd[b] : 0.f;
@@ -285,8 +300,9 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
     }
 }
 
-template <int DT, int MAXV, bool BWD>
-__global__ void __launch_bounds__(kMaxBlock, LF_MIN_BLOCKS) render_kernel(const __grid_constant__ RenderParams<MAXV> p)
+template <int DT, int MAXV, bool BWD, int K>
+__global__ void __launch_bounds__(kMaxBlock, K == 5 ? LF_MIN_BLOCKS : 2)
+    render_kernel(const __grid_constant__ RenderParams<MAXV> p)
 {
     __shared__ uint32_t s_tile[4];     // view, tile column, tile row, valid
     const uint32_t nv = p.n_views;
@@ -309,9 +325,9 @@ __global__ void __launch_bounds__(kMaxBlock, LF_MIN_BLOCKS) render_kernel(const 
         const ViewK &vw = p.views[v];
         bool active = px < vw.width && py < vw.height;
         if constexpr (BWD) {
-            backward_ray(p, &vw, active, px, py);
+            backward_ray<K>(p, &vw, active, px, py);
         } else {
-            if (active) render_ray<DT>(p, vw, px, py);
+            if (active) render_ray<DT, K>(p, vw, px, py);
         }
         if (!p.persistent) break;
         __syncthreads();               // everyone has read s_tile before it is rewritten
@@ -326,33 +342,41 @@ __global__ void __launch_bounds__(kMaxBlock, LF_MIN_BLOCKS) render_kernel(const 
     }
 }
 
-template <int MAXV>
-static cudaError_t launch_t(int kind, bool bwd, const RenderParams<MAXV> &p, unsigned grid,
-                            unsigned block, cudaStream_t st)
+template <int MAXV, int K>
+static cudaError_t launch_k(int kind, bool bwd, const RenderParams<MAXV> &p, unsigned grid, unsigned block,
+                            cudaStream_t st)
 {
     if (bwd) {
-        render_kernel<kF32C4, MAXV, true><<<grid, block, 0, st>>>(p);
+        render_kernel<kF32C4, MAXV, true, K><<<grid, block, 0, st>>>(p);
     } else {
         switch (kind) {
-        case kF32C4: render_kernel<kF32C4, MAXV, false><<<grid, block, 0, st>>>(p); break;
-        case kF32C3: render_kernel<kF32C3, MAXV, false><<<grid, block, 0, st>>>(p); break;
-        case kF16C4: render_kernel<kF16C4, MAXV, false><<<grid, block, 0, st>>>(p); break;
-        default: render_kernel<kE4M3C4, MAXV, false><<<grid, block, 0, st>>>(p); break;
+        case kF32C4: render_kernel<kF32C4, MAXV, false, K><<<grid, block, 0, st>>>(p); break;
+        case kF32C3: render_kernel<kF32C3, MAXV, false, K><<<grid, block, 0, st>>>(p); break;
+        case kF16C4: render_kernel<kF16C4, MAXV, false, K><<<grid, block, 0, st>>>(p); break;
+        default: render_kernel<kE4M3C4, MAXV, false, K><<<grid, block, 0, st>>>(p); break;
         }
     }
     return cudaGetLastError();
 }
 
 template <int MAXV>
-static int occupancy_t(int kind, bool bwd, unsigned block)
+static cudaError_t launch_t(int kind, bool bwd, const RenderParams<MAXV> &p, unsigned grid,
+                            unsigned block, cudaStream_t st)
+{
+    return p.nine ? launch_k<MAXV, 9>(kind, bwd, p, grid, block, st)
+                  : launch_k<MAXV, 5>(kind, bwd, p, grid, block, st);
+}
+
+template <int MAXV, int K>
+static int occupancy_k(int kind, bool bwd, unsigned block)
 {
     int n = 0;
     const void *f;
-    if (bwd) f = (const void *)render_kernel<kF32C4, MAXV, true>;
-    else if (kind == kF32C4) f = (const void *)render_kernel<kF32C4, MAXV, false>;
-    else if (kind == kF32C3) f = (const void *)render_kernel<kF32C3, MAXV, false>;
-    else if (kind == kF16C4) f = (const void *)render_kernel<kF16C4, MAXV, false>;
-    else f = (const void *)render_kernel<kE4M3C4, MAXV, false>;
+    if (bwd) f = (const void *)render_kernel<kF32C4, MAXV, true, K>;
+    else if (kind == kF32C4) f = (const void *)render_kernel<kF32C4, MAXV, false, K>;
+    else if (kind == kF32C3) f = (const void *)render_kernel<kF32C3, MAXV, false, K>;
+    else if (kind == kF16C4) f = (const void *)render_kernel<kF16C4, MAXV, false, K>;
+    else f = (const void *)render_kernel<kE4M3C4, MAXV, false, K>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, (int)block, 0) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
 }
@@ -367,9 +391,11 @@ cudaError_t launch_render_large(int kind, bool bwd, const RenderParams<kLargeVie
 {
     return launch_t<kLargeViews>(kind, bwd, p, grid, block, st);
 }
-int render_occupancy(int kind, bool bwd, bool large, unsigned block)
+int render_occupancy(int kind, bool bwd, bool large, bool nine, unsigned block)
 {
-    return large ? occupancy_t<kLargeViews>(kind, bwd, block) : occupancy_t<kSmallViews>(kind, bwd, block);
+    if (nine)
+        return large ? occupancy_k<kLargeViews, 9>(kind, bwd, block) : occupancy_k<kSmallViews, 9>(kind, bwd, block);
+    return large ? occupancy_k<kLargeViews, 5>(kind, bwd, block) : occupancy_k<kSmallViews, 5>(kind, bwd, block);
 }
 
 }  // namespace lfk

@@ -62,7 +62,7 @@ class LightField:
         desc.dtype = lp.DTYPES[dtype]
         desc.flags = (lp.LF_TABLE_BORROW if borrow else 0) | (lp.LF_TABLE_UPPER_HEMISPHERE if upper else 0)
         desc.k_nearest = int(k_nearest)
-        self.K = int(k_nearest)
+        self.K = int(k_nearest) or 5
         self.M, self.N, self.C, self.dtype, self.R, self.O = M, N, Cc, dtype, float(R), tuple(O)
         self.rows, self.upper = rows, bool(upper)
         self._keep = (radiance, scales) if borrow else None

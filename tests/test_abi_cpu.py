@@ -75,7 +75,8 @@ def _desc(**kw):
     (dict(dtype=7), lp.LF_ERR_INVALID_ARG),
     (dict(dtype=1), lp.LF_ERR_INVALID_ARG),          # F16 without scales
     (dict(flags=0x80), lp.LF_ERR_INVALID_ARG),
-    (dict(k=9), lp.LF_ERR_UNSUPPORTED),
+    (dict(k=7), lp.LF_ERR_UNSUPPORTED),
+    (dict(k=16), lp.LF_ERR_UNSUPPORTED),
 ])
 def test_create_table_rejects_bad_descriptions(kw, status):
     h = C.c_void_p(123)

@@ -439,3 +439,42 @@ def test_upper_hemisphere_mode():
     w = oracle.tent_weights_kept(np.array([0.0, 0.01, 0.02, 0.03, 0.04]) ** 2,
                                  np.array([300, 10, 250, 20, 30]), M, M // 2)
     assert w[0] == 0 and w[2] == 0 and abs(w.sum() - 1) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Continuous lobe field (the reference of interpolation quality per K)
+# --------------------------------------------------------------------------
+def test_continuous_lobe_field_samples_to_the_table():
+    # at the SF points and the chord direction the field plus the texel's noise is the texel
+    lob = lf_inputs.draw_lobes(4, 6, 4)
+    M, N = 300, 70
+    Po, Pd = oracle.sf_points(M), oracle.sf_points(N)
+    for i, j in [(0, 0), (17, 3), (299, 69), (150, 35)]:
+        d = Pd[j] - Po[i]
+        d /= np.linalg.norm(d)
+        cont = oracle.lobe_continuous(lob, Po[i], d)
+        noise = np.array([0.01 * (oracle.splitmix64(lob.noise_seed, (i << 32) | (j << 4) | c) >> 11) * 2.0 ** -53
+                          for c in range(4)])
+        np.testing.assert_allclose(cont + noise, oracle.lobe_texel(lob, M, N, i, j), rtol=0, atol=1e-15)
+
+
+def test_continuous_lobe_field_peak_and_antipode():
+    lob = lf_inputs.draw_lobes(8, 1, 3)
+    a, b = lob.ap[0], lob.ad[0]
+    # a . a = 1 to rounding, so the peak is exact to a few ulp of kp + kd
+    np.testing.assert_allclose(oracle.lobe_continuous(lob, a, b), lob.col[0], rtol=1e-14, atol=0)
+    want = lob.col[0] * math.exp(-2 * lob.kp[0]) * math.exp(-2 * lob.kd[0])
+    np.testing.assert_allclose(oracle.lobe_continuous(lob, -a, -b), want, rtol=1e-13, atol=0)
+
+
+def test_reference_pixels_follow_the_ray():
+    lob = lf_inputs.draw_lobes(2, 5, 3)
+    v = lf_inputs.look_at((2.5, 0.4, -0.3), (0, 0, 0), 40, 30)
+    pix = lf_inputs.pixel_list([v])
+    out, hit = oracle.lobe_reference_pixels(lob, [v], pix)
+    assert 0 < hit.sum() < len(pix)
+    for k in np.nonzero(hit)[0][::97]:
+        _, _, _, _, qo, qd = oracle.trace_pixel(1.0, (0, 0, 0), v, pix[k, 1], pix[k, 2])
+        u = (qd - qo) / np.linalg.norm(qd - qo)
+        np.testing.assert_allclose(out[k], oracle.lobe_continuous(lob, qo, u), rtol=0, atol=1e-15)
+    assert np.all(out[~hit] == 0)
