@@ -622,7 +622,8 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
 // keeps its threshold of 16). Ranking: tier-1 keys (5 slot bits) of all
 // candidates into a sorted list of the 10 smallest; when each of the top 10
 // lies below the next by more than the tier-1 error plus 2^-40, the order and
-// membership of the top 9 are exact; otherwise FP64 by (distance, index).
+// membership of the top 9 are exact; otherwise tier 2 re-ranks the top 10 in
+// double-float, and FP64 settles what is still uncertain.
 // ---------------------------------------------------------------------------
 constexpr int kWindow9 = 25;
 
@@ -680,6 +681,62 @@ __device__ __noinline__ TopK<9> knn9_fp64(const PointSetK P, const SphereK S, fl
     return r;
 }
 
+// Tier 2 of the 9 nearest (rare: the tier-1 order was not certain): the top 10
+// in double-float, sorted (4 slot bits), accepted when every consecutive gap of
+// the top 10 exceeds the tier-2 error (2^-18 d^2 + 2^-40, as for 5 neighbours);
+// otherwise FP64 by (distance, index). Out of line: the common path keeps its
+// registers.
+struct Keys10 {
+    uint32_t k[10];
+};
+
+__device__ __noinline__ TopK<9> knn9_rerank(const PointSetK P, const SphereK S, float3 h, const Source src,
+                                            float3 qh, float3 ql, const Keys10 s10, uint32_t mask1)
+{
+    constexpr uint32_t kNone = 0xffffffffu;
+    uint32_t k10[10];
+    int32_t id10[10];
+    float dd10[10];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) {
+        bool ok = s10.k[m] != kNone;
+        int32_t i = ok ? source_index9(src, (int)(s10.k[m] & mask1)) : 0;
+        id10[m] = i;
+        dd10[m] = dist2_df(P, i, qh, ql);
+        k10[m] = kNone;
+    }
+#pragma unroll
+    for (int m = 0; m < 10; ++m)
+        insert_sorted(k10, s10.k[m] != kNone ? ((__float_as_uint(dd10[m]) & ~15u) | (uint32_t)m) : kNone);
+    bool exact = true;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+        if (k10[m + 1] != kNone) {
+            float a = __uint_as_float(k10[m] & ~15u), b = __uint_as_float(k10[m + 1] & ~15u);
+            exact &= (b - a) > __fmaf_rn(0x1p-18f, b, 0x1p-40f);
+        }
+    }
+    if (!exact) return knn9_fp64(P, S, h, src, qh, ql);
+    TopK<9> r;
+    r.cnt = 0;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+        bool ok = k10[m] != kNone;
+        int sl = (int)(k10[m] & 15u);
+        int32_t i = id10[0];
+        float dd = dd10[0];
+#pragma unroll
+        for (int c = 1; c < 10; ++c) {
+            i = (sl == c) ? id10[c] : i;
+            dd = (sl == c) ? dd10[c] : dd;
+        }
+        r.i[m] = ok ? i : -1;
+        r.d2[m] = ok ? dd : 0.0f;
+        r.cnt += ok ? 1 : 0;
+    }
+    return r;
+}
+
 // The 9 nearest points of the unit hit in (distance, index) order with their
 // double-float squared distances; cnt = min(9, n).
 __device__ __forceinline__ TopK<9> knn9(const PointSetK &P, const SphereK &S, float3 h, uint32_t *status)
@@ -729,7 +786,12 @@ __device__ __forceinline__ TopK<9> knn9(const PointSetK &P, const SphereK &S, fl
         r.d2[m] = ok ? dist2_df(P, i, qh, ql) : 0.0f;
         r.cnt += ok ? 1 : 0;
     }
-    if (!order1) r = knn9_fp64(P, S, h, src, qh, ql);
+    if (!order1) {
+        Keys10 keys;
+#pragma unroll
+        for (int m = 0; m < 10; ++m) keys.k[m] = s10[m];
+        r = knn9_rerank(P, S, h, src, qh, ql, keys, mask1);
+    }
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
         if (m < r.cnt && (uint32_t)r.i[m] >= (uint32_t)n) {   // impossible by construction; recorded, never trapped

@@ -148,6 +148,11 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
         // loop rolled (instruction-cache footprint).
 #pragma unroll(K == 5 ? 5 : 1)
         for (int a = 0; a < K; ++a) {
+            // Nine neighbours: the tent gives the outer ones weight 0 almost always;
+            // their taps are skipped (a branch that whole warps take together).
+            if constexpr (K == 9) {
+                if (wo[a] == 0.0f) continue;
+            }
             // a missing or unstored neighbour has weight 0 and reads row 0
             int32_t i = (uint32_t)io[a] < p.rows_valid ? io[a] : 0;
             float s = wo[a];
@@ -156,6 +161,9 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
             float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
 #pragma unroll
             for (int b = 0; b < K; ++b) {
+                if constexpr (K == 9) {
+                    if (wd[b] == 0.0f) continue;
+                }
                 float4 t = texel<DT>(p.texels, row + (uint32_t)max(jd[b], 0));
                 float2 w2 = make_float2(wd[b], wd[b]);
                 in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
