@@ -219,6 +219,31 @@ def test_index_step_large_sets_sampled(api, M, N):
     assert mism.sum() == 0, f"{mism.sum()} of {len(pix)} rays differ"
 
 
+@pytest.mark.parametrize("M,N", [(1 << 24, 4), (3, 1 << 24)])
+def test_index_step_maximum_point_counts(api, M, N):
+    """The largest sets the boundary accepts (2^24 points): FP32 lattice
+    coordinates of a 16.7 M-point set against brute force on sampled rays."""
+    views = lf_inputs.pack_offsets([lf_inputs.look_at((1.7, 0.6, -0.9), (0, 0, 0), 320, 240),
+                                    lf_inputs.look_at((0.03, 0.01, 2.4), (0, 0, 0), 64, 64),
+                                    lf_inputs.look_at((0.02, -0.04, -2.1), (0, 0, 0), 64, 64)])
+    codes = torch.zeros((M, N, 4), dtype=torch.uint8, device="cuda")
+    scales = torch.ones((M,), dtype=torch.float32, device="cuda")
+    lf = api.LightField(codes, "e4m3", scales, borrow=True)
+    _, idx = lf.render(views, with_idx=True)
+    lf.sync_status()
+    idx = idx.cpu().numpy()
+    lf.close()
+    del codes
+    torch.cuda.empty_cache()
+    pix = lf_inputs.sample_pixels(views, 500, seed=M + N)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    sc = oracle.Scene(M, N, 4, "lobe", lobes=lf_inputs.draw_lobes(0, 0, 4))
+    _, want_idx, hits = oracle.render_pixels(sc, views, pix)
+    mism = np.any(idx[offs] != want_idx, axis=1)
+    assert hits > 100
+    assert mism.sum() == 0, f"{mism.sum()} of {len(pix)} rays differ"
+
+
 # --------------------------------------------------------------------------
 # Backward: oracle gradient, adjoint identity, finite differences
 # --------------------------------------------------------------------------
