@@ -361,7 +361,7 @@ def run_ours(args, rank: int, world: int):
                        "memory every frame on a second stream (double-buffered); median of 3 "
                        "windows of K frames",
                 "windows_grays_s": [world * args.steps * rays / w / 1e9 for w in e2e_windows],
-                "d2h_copy_gbs": d2h_gbs, "copy_bound_grays_s": world * d2h_gbs * 1e9 / (rays * 16) / 1e9},
+                "d2h_copy_gbs": d2h_gbs, "copy_bound_grays_s": world * d2h_gbs / 16.0},
         "gpu_launches": args.steps,
         "variants": variants,
         "psnr_vs_f32_table_db": psnr_vs_f32,
