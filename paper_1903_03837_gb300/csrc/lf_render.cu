@@ -148,14 +148,24 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
         // loop rolled (instruction-cache footprint).
 #pragma unroll(K == 5 ? 5 : 1)
         for (int a = 0; a < K; ++a) {
+            // origin neighbour a by a select chain: with the loop rolled (K = 9) a
+            // run-time index would move the arrays to local memory; unrolled (K = 5)
+            // the chain folds away
+            int32_t ia = io[0];
+            float wa = wo[0];
+#pragma unroll
+            for (int m = 1; m < K; ++m) {
+                ia = (a == m) ? io[m] : ia;
+                wa = (a == m) ? wo[m] : wa;
+            }
             // Nine neighbours: the tent gives the outer ones weight 0 almost always;
             // their taps are skipped (a branch that whole warps take together).
             if constexpr (K == 9) {
-                if (wo[a] == 0.0f) continue;
+                if (wa == 0.0f) continue;
             }
             // a missing or unstored neighbour has weight 0 and reads row 0
-            int32_t i = (uint32_t)io[a] < p.rows_valid ? io[a] : 0;
-            float s = wo[a];
+            int32_t i = (uint32_t)ia < p.rows_valid ? ia : 0;
+            float s = wa;
             if constexpr (DT == kF16C4 || DT == kE4M3C4) s *= __ldg(p.scales + i);
             size_t row = (size_t)i * p.N;
             float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
@@ -259,7 +269,9 @@ __device__ __forceinline__ void add_to_grad(const RenderParamsBase &p, uint64_t 
 // hold the same texel key are summed first (warp aggregation): when every live
 // lane of the warp has the same key, a butterfly over the warp and one atomic;
 // otherwise __match_any_sync groups and a tree sum per group, one atomic per
-// group. The tap loop stays rolled (instruction-cache footprint).
+// group. The loop over origin neighbours stays rolled (instruction-cache
+// footprint), the K direction taps inside it are unrolled so that the
+// neighbour arrays stay in registers.
 template <int K>
 __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const ViewK *v, bool active,
                                              uint32_t px, uint32_t py)
@@ -281,32 +293,44 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
     const unsigned lane = threadIdx.x & 31;
     if (!__any_sync(0xffffffffu, hit)) return;
 #pragma unroll 1
-    for (int t = 0; t < K * K; ++t) {
-        const int a = t / K, b = t - K * (t / K);
-        bool live = hit && (uint32_t)io[a] < p.rows_valid && jd[b] >= 0;
-        uint64_t key = live ? (uint64_t)io[a] * p.N + (uint64_t)jd[b] : 0ull;
-        float W = live ? wo[a] * wd[b] : 0.f;
-        float4 val = make_float4(W * g.x, W * g.y, W * g.z, W * g.w);
-        unsigned live_mask = __ballot_sync(0xffffffffu, live);
-        if (live_mask == 0u) continue;
-        const int leader = __ffs(live_mask) - 1;
-        uint64_t lkey = __shfl_sync(0xffffffffu, key, leader);
-        if (__all_sync(0xffffffffu, !live || key == lkey)) {
+    for (int a = 0; a < K; ++a) {
+        // this origin neighbour by a select chain (a run-time index into the
+        // register arrays would move them to local memory)
+        int32_t ia = io[0];
+        float wa = wo[0];
 #pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                val.x += __shfl_xor_sync(0xffffffffu, val.x, s);
-                val.y += __shfl_xor_sync(0xffffffffu, val.y, s);
-                val.z += __shfl_xor_sync(0xffffffffu, val.z, s);
-                val.w += __shfl_xor_sync(0xffffffffu, val.w, s);
+        for (int m = 1; m < K; ++m) {
+            ia = (a == m) ? io[m] : ia;
+            wa = (a == m) ? wo[m] : wa;
+        }
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            bool live = hit && (uint32_t)ia < p.rows_valid && jd[b] >= 0;
+            uint64_t key = live ? (uint64_t)ia * p.N + (uint64_t)jd[b] : 0ull;
+            float W = live ? wa * wd[b] : 0.f;
+            float4 val = make_float4(W * g.x, W * g.y, W * g.z, W * g.w);
+            unsigned live_mask = __ballot_sync(0xffffffffu, live);
+            if (live_mask == 0u) continue;
+            const int leader = __ffs(live_mask) - 1;
+            uint64_t lkey = __shfl_sync(0xffffffffu, key, leader);
+            if (__all_sync(0xffffffffu, !live || key == lkey)) {
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    val.x += __shfl_xor_sync(0xffffffffu, val.x, s);
+                    val.y += __shfl_xor_sync(0xffffffffu, val.y, s);
+                    val.z += __shfl_xor_sync(0xffffffffu, val.z, s);
+                    val.w += __shfl_xor_sync(0xffffffffu, val.w, s);
+                }
+                if ((int)lane == leader) add_to_grad(p, lkey, val);
+            } else {
+                unsigned grp = __match_any_sync(0xffffffffu, live ? key : ~0ull - lane);
+                float4 sum = group_sum_tree(val, grp, lane);
+                if (live && (__ffs(grp) - 1) == (int)lane) add_to_grad(p, key, sum);
             }
-            if ((int)lane == leader) add_to_grad(p, lkey, val);
-        } else {
-            unsigned grp = __match_any_sync(0xffffffffu, live ? key : ~0ull - lane);
-            float4 sum = group_sum_tree(val, grp, lane);
-            if (live && (__ffs(grp) - 1) == (int)lane) add_to_grad(p, key, sum);
         }
     }
 }
+
 
 template <int DT, int MAXV, bool BWD, int K>
 __global__ void __launch_bounds__(kMaxBlock, K == 5 ? LF_MIN_BLOCKS : 2)
