@@ -610,7 +610,13 @@ def cpu_baseline(cfg, views, gpu_images, args, k_images=None):
         for k, img in k_images.items():
             g = img.cpu().numpy().astype(np.float64)[offs]
             psnr_k[k] = oracle.psnr(cont, g, chit & hit)
+    # one host thread on a smaller sample (single-thread rate of the same oracle)
+    pix1 = lf_inputs.sample_pixels(views, max(500, int(rate / cores * 2.0)), seed=13)
+    t1 = time.perf_counter()
+    oracle.render_pixels(sc, views, pix1, threads=1)
+    single = len(pix1) / (time.perf_counter() - t1)
     base = {"value": n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": single / 1e9,
             "sample": f"{n:,} random pixels of orbit frame 0 ({hits:,} hits), brute-force FP64 K-NN "
                       f"over all {cfg.M:,}+{cfg.N:,} SF points, texels from the FP64 lobe field; "
                       f"{dt:.1f} s on {cores} threads"}
