@@ -453,8 +453,10 @@ def run_precompute(args):
 
 def run_fit_steps(args):
     """Differentiation workload: 16,384 x 512 RGB FP32 table, 32 target views of
-    512x512; one step = render (forward kernel) + MSE + backward scatter kernel +
-    Adam on the FP32 table. Times the steps and the backward launches alone."""
+    512x512; one step = render (forward kernel, writing its sample indices) + MSE
+    + backward scatter kernel from those indices + Adam on the FP32 table. Times
+    the steps and the backward launches alone, and once more the backward that
+    searches the indices again (lf_render_backward)."""
     import torch
     from paper_1903_03837_gb300 import torch_api as api
     cfg = lf_inputs.config_differentiation()
@@ -468,15 +470,16 @@ def run_fit_steps(args):
     opt = torch.optim.Adam([table], lr=cfg.extra["lr"])
     st = torch.cuda.current_stream()
     bwd_ms = []
+    idx = torch.empty((rays, 2 * lf.K), dtype=torch.int32, device="cuda")
 
     def step(timed):
         opt.zero_grad(set_to_none=False)
-        img, _ = lf.render(train)
+        img, _ = lf.render(train, idx=idx)
         g = (2.0 / img.numel()) * (img - target)
         if timed:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
-        lf.render_backward(train, g, table.grad)
+        lf.render_backward(train, g, table.grad, idx=idx)
         if timed:
             b.record(st)
             bwd_ms.append((a, b))
@@ -492,12 +495,24 @@ def run_fit_steps(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     bms = sum(a.elapsed_time(b) for a, b in bwd_ms) / len(bwd_ms)
+    # the backward that searches again, for comparison (same gradient buffer, same frame)
+    g = (2.0 / target.numel()) * (lf.render(train)[0] - target)
+    for _ in range(2):
+        lf.render_backward(train, g, table.grad)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(5):
+        lf.render_backward(train, g, table.grad)
+    b.record(st)
+    torch.cuda.synchronize()
+    bms_search = a.elapsed_time(b) / 5
     lf.close()
     lf_gt.close()
     return {"workload": f"differentiation: {cfg.M:,} x {cfg.N:,} RGB FP32 table, {len(train)} views 512x512 "
                         f"({rays:,} rays), Adam lr 1e-2",
             "ms_per_fit_step": ms, "fit_steps_per_s": 1e3 / ms,
             "backward_ms": bms, "backward_grays_s": rays / (bms * 1e-3) / 1e9,
+            "backward_search_ms": bms_search,
             "fwd_bwd_adam_grays_s": rays / (ms * 1e-3) / 1e9}
 
 

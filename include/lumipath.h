@@ -148,6 +148,19 @@ lf_status lf_render(const lf_table *t, const lf_view *views_host, uint32_t n_vie
 lf_status lf_render_backward(const lf_table *t, const lf_view *views_host, uint32_t n_views,
                              const float *grad_out_dev, float *grad_table_dev, void *stream);
 
+/* The same gradient from the sample indices a render of the same views wrote
+ * (idx_dev: device int32 [P][2K] as lf_render writes them, [P][2] with nearest
+ * sampling), instead of a new index step: the hits, the unit hits and the
+ * double-float distances of these indices are recomputed, the same distances by
+ * the same function as the index step's, so the weights are identical and a
+ * fit that keeps its forward indices skips the search in the backward. A miss
+ * (index -1) contributes nothing; an index out of range counts as missing and
+ * makes the next lf_sync_status report LF_ERR_DEVICE_CHECK.
+ * Errors: LF_ERR_INVALID_ARG, LF_ERR_CUDA. */
+lf_status lf_render_backward_idx(const lf_table *t, const lf_view *views_host, uint32_t n_views,
+                                 const float *grad_out_dev, const int32_t *idx_dev, float *grad_table_dev,
+                                 void *stream);
+
 /* Destroy a table (NULL-safe). Synchronises the device before freeing. */
 void lf_destroy(lf_table *t);
 

@@ -149,7 +149,7 @@ lf_status run_chunk(const lf_table *t, const lfk::RenderParamsBase &base, const 
 }
 
 lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *out, int32_t *idx,
-              const float *grad_out, float *grad, void *stream)
+              const float *grad_out, float *grad, void *stream, const int32_t *idx_in = nullptr)
 {
     lf_status s = check_views(views, n_views);
     if (s != LF_OK) return s;
@@ -167,6 +167,7 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
     b.C = t->C;
     b.out = out;
     b.idx = idx;
+    b.idx_in = idx_in;
     b.grad_out = grad_out;
     b.grad = grad;
     b.status = t->scratch;
@@ -394,6 +395,17 @@ lf_status lf_render_backward(const lf_table *t, const lf_view *views, uint32_t n
     if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
     if (!grad_out_dev || !grad_table_dev) return fail(LF_ERR_INVALID_ARG, "gradient buffer is NULL");
     return run(t, views, n_views, nullptr, nullptr, grad_out_dev, grad_table_dev, stream);
+}
+
+lf_status lf_render_backward_idx(const lf_table *t, const lf_view *views, uint32_t n_views,
+                                 const float *grad_out_dev, const int32_t *idx_dev, float *grad_table_dev,
+                                 void *stream)
+{
+    g_err.clear();
+    if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
+    if (!grad_out_dev || !grad_table_dev) return fail(LF_ERR_INVALID_ARG, "gradient buffer is NULL");
+    if (!idx_dev) return fail(LF_ERR_INVALID_ARG, "idx is NULL");
+    return run(t, views, n_views, nullptr, nullptr, grad_out_dev, grad_table_dev, stream, idx_dev);
 }
 
 lf_status lf_sync_status(lf_table *t, void *stream)

@@ -21,7 +21,8 @@ struct RenderParamsBase {
     uint32_t N;                    // texels per origin row
     uint32_t C;                    // output / gradient channels (3 or 4)
     float *out;                    // forward: [P][C]
-    int32_t *idx;                  // forward: [P][10] or NULL
+    int32_t *idx;                  // forward: [P][2K] or NULL
+    const int32_t *idx_in;         // backward: the forward's [P][2K] indices, or NULL (search again)
     const float *grad_out;         // backward: [P][C]
     float *grad;                   // backward: [M][N][C]
     uint32_t *status, *queue, *done;

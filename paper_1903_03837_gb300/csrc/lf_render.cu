@@ -122,6 +122,73 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
     return true;
 }
 
+// The samples of one ray from the indices a forward pass wrote for it (idx_in:
+// [P][2K], or [P][2] with nearest sampling): the hits and unit hits are
+// recomputed and the weights formed from the double-float distances of these
+// indices -- the same distances, by the same function, as the index step's, so
+// the weights are identical. An index out of range counts as missing and sets
+// bit 0 of the status word; a ray the indices call a hit but that misses S sets
+// bit 1.
+template <int K>
+__device__ __forceinline__ bool samples_from_idx(const RenderParamsBase &p, const ViewK &v, uint32_t px,
+                                                 uint32_t py, uint64_t pix, int32_t (&io)[K], int32_t (&jd)[K],
+                                                 float (&wo)[K], float (&wd)[K])
+{
+    const int32_t *q = p.idx_in + pix * (uint64_t)(p.nearest_only ? 2 : 2 * K);
+#pragma unroll
+    for (int m = 0; m < K; ++m) io[m] = jd[m] = -1;
+    if (p.nearest_only) {
+        io[0] = __ldg(q);
+        jd[0] = __ldg(q + 1);
+    } else {
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            io[m] = __ldg(q + m);
+            jd[m] = __ldg(q + K + m);
+        }
+    }
+    if (io[0] < 0) return false;
+    float3 d = camera_dir(v, px, py);
+    float3 ho, hd;
+    if (!intersect_sphere(p.sphere, v.eye, d, ho, hd)) {
+        atomicOr(p.status, 2u);
+        return false;
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        PointSetK P;
+        P.hi = s ? p.pd.hi : p.po.hi;
+        P.lo = s ? p.pd.lo : p.po.lo;
+        P.n = s ? p.pd.n : p.po.n;
+        P.inv_sigma = s ? p.pd.inv_sigma : p.po.inv_sigma;
+        int32_t (&ix)[K] = s ? jd : io;
+        float(&w)[K] = s ? wd : wo;
+        float3 qh, ql;
+        unit_hit_df(p.sphere, s ? hd : ho, qh, ql);
+        float d2[K];
+        int cnt = 0;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            const bool ok = (uint32_t)ix[m] < P.n;
+            if (!ok && ix[m] >= 0) {
+                atomicOr(p.status, 1u);
+                ix[m] = -1;
+            }
+            d2[m] = ok ? dist2_df(P, ok ? ix[m] : 0, qh, ql) : 0.0f;
+            cnt += ok ? 1 : 0;
+        }
+        if (p.nearest_only) {
+#pragma unroll
+            for (int m = 0; m < K; ++m) w[m] = m == 0 ? 1.0f : 0.0f;
+        } else if (s == 0 && p.rows_stored) {
+            if (!tent_weights_kept(d2, ix, cnt, P.inv_sigma, p.rows_stored, w)) return false;
+        } else {
+            tent_weights(d2, cnt, P.inv_sigma, w);
+        }
+    }
+    return true;
+}
+
 // Packed FP32 pair FMA (one instruction for two lanes of a texel).
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
 {
@@ -281,8 +348,9 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
     bool hit = false;
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) {
-        hit = !certain_miss(*v, px, py) && ray_samples(p, *v, px, py, io, jd, wo, wd);
         uint64_t pix = v->out_offset + (uint64_t)py * v->width + px;
+        hit = p.idx_in ? samples_from_idx<K>(p, *v, px, py, pix, io, jd, wo, wd)
+                       : (!certain_miss(*v, px, py) && ray_samples<K>(p, *v, px, py, io, jd, wo, wd));
         if (p.C == 4) {
             g = __ldg(reinterpret_cast<const float4 *>(p.grad_out) + pix);
         } else {

@@ -84,6 +84,7 @@ def lib():
                 "lf_create_table": (st, [C.POINTER(lf_table_desc), vp, vp, vp, C.POINTER(vp)]),
                 "lf_render": (st, [vp, C.POINTER(lf_view), u32, vp, vp, vp]),
                 "lf_render_backward": (st, [vp, C.POINTER(lf_view), u32, vp, vp, vp]),
+                "lf_render_backward_idx": (st, [vp, C.POINTER(lf_view), u32, vp, vp, vp, vp]),
                 "lf_destroy": (None, [vp]),
                 "lf_last_error": (C.c_char_p, []),
                 "lf_set_launch": (st, [vp, C.POINTER(lf_launch)]),
@@ -153,6 +154,13 @@ def lf_render_backward(table: int, views, n_views: int, grad_out_ptr: int, grad_
                        stream: int = 0):
     _check(lib().lf_render_backward(C.c_void_p(table), views, n_views, C.c_void_p(grad_out_ptr),
                                     C.c_void_p(grad_table_ptr), C.c_void_p(stream or None)))
+
+
+def lf_render_backward_idx(table: int, views, n_views: int, grad_out_ptr: int, idx_ptr: int,
+                           grad_table_ptr: int, stream: int = 0):
+    _check(lib().lf_render_backward_idx(C.c_void_p(table), views, n_views, C.c_void_p(grad_out_ptr),
+                                        C.c_void_p(idx_ptr), C.c_void_p(grad_table_ptr),
+                                        C.c_void_p(stream or None)))
 
 
 def lf_destroy(table: Optional[int]):

@@ -98,7 +98,11 @@ class LightField:
         return out, idx
 
     def render_backward(self, views: Sequence, grad_out: torch.Tensor,
-                        grad_table: Optional[torch.Tensor] = None) -> torch.Tensor:
+                        grad_table: Optional[torch.Tensor] = None,
+                        idx: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Accumulate d(loss)/d(table) into grad_table. With `idx` (the int32
+        [P, 2K] indices a render of the same views wrote), the backward reuses
+        them instead of searching again (lf_render_backward_idx)."""
         _need_cuda(grad_out, "grad_out")
         if grad_out.dtype != torch.float32 or grad_out.numel() < total_pixels(views) * self.C:
             raise ValueError("grad_out must be float32 [P, C]")
@@ -108,7 +112,15 @@ class LightField:
         if grad_table.dtype != torch.float32 or grad_table.numel() != self.rows * self.N * self.C:
             raise ValueError("grad_table must be float32 [rows, N, C]")
         vv = lp.make_views(views)
-        lp.lf_render_backward(self.handle, vv, len(views), grad_out.data_ptr(), grad_table.data_ptr(), _stream())
+        if idx is not None:
+            _need_cuda(idx, "idx")
+            if idx.dtype != torch.int32 or not idx.is_contiguous() or idx.numel() < total_pixels(views) * 2 * self.K:
+                raise ValueError("idx must be a contiguous int32 tensor of at least P * 2K elements")
+            lp.lf_render_backward_idx(self.handle, vv, len(views), grad_out.data_ptr(), idx.data_ptr(),
+                                      grad_table.data_ptr(), _stream())
+        else:
+            lp.lf_render_backward(self.handle, vv, len(views), grad_out.data_ptr(), grad_table.data_ptr(),
+                                  _stream())
         return grad_table
 
     def sync_status(self):
@@ -135,12 +147,14 @@ class RenderFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, table: torch.Tensor, lf: LightField, views):
         ctx.lf, ctx.views = lf, views
-        out, _ = lf.render(views)
+        out, idx = lf.render(views, with_idx=True)      # the backward reuses the indices
+        ctx.idx = idx
         return out
 
     @staticmethod
     def backward(ctx, grad):
-        g = ctx.lf.render_backward(ctx.views, grad.contiguous())
+        g = ctx.lf.render_backward(ctx.views, grad.contiguous(), idx=ctx.idx)
+        ctx.idx = None
         return g, None, None
 
 

@@ -418,3 +418,61 @@ def test_nearest_sampling_mode(api, M, N, upper):
     assert got[1].shape == (lf_inputs.total_pixels(views), 2)
     check_parity(got, (want_out, want_idx))
     lf.close()
+
+
+# --------------------------------------------------------------------------
+# Backward from the forward's indices (lf_render_backward_idx)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["rgba", "rgb", "upper", "nearest", "nine"])
+def test_backward_from_indices_equals_search(api, case):
+    M, N, Cc, upper, K = 1024, 256, 4, False, 5
+    if case == "rgb":
+        Cc = 3
+    if case == "upper":
+        M, upper = 3001, True
+    if case == "nearest":
+        K = 1
+    if case == "nine":
+        K = 9
+    rows = M // 2 if upper else M
+    rng = np.random.default_rng(len(case))
+    T = rng.uniform(0, 1, (rows, N, Cc)).astype(np.float32)
+    views = lf_inputs.pack_offsets([lf_inputs.look_at((2.4, 0.3, 0.4), (0, 0, 0), 96, 80),
+                                    lf_inputs.look_at((0.1, 0.05, 2.6), (0, 0, 0), 48, 48)])
+    lf = api.LightField(torch.from_numpy(T).cuda(), "f32", n_origins=M, upper=upper, k_nearest=K)
+    P = lf_inputs.total_pixels(views)
+    g = torch.from_numpy(rng.standard_normal((P, Cc)).astype(np.float32)).cuda()
+    _, idx = lf.render(views, with_idx=True)
+    G_idx = lf.render_backward(views, g, idx=idx).cpu().numpy().astype(np.float64)
+    G_srch = lf.render_backward(views, g).cpu().numpy().astype(np.float64)
+    lf.sync_status()
+    # the same weights; only the order of the atomic additions differs
+    assert np.abs(G_idx - G_srch).max() <= 1e-5 * max(1.0, np.abs(G_srch).max())
+    pix = lf_inputs.pixel_list(views)
+    offs = lf_inputs.pixel_offsets(views, pix)
+    Gw = oracle.render_backward(oracle.Scene(M, N, Cc, "f32", T, K=K, upper=upper), views, pix,
+                                g.cpu().numpy()[offs].astype(np.float64))
+    assert np.abs(G_idx - Gw).max() <= 2e-5 * max(1.0, np.abs(Gw).max())
+    assert np.abs(Gw).max() > 0
+    lf.close()
+
+
+def test_backward_from_indices_rejects_bad_indices(api):
+    from paper_1903_03837_gb300 import lumipath as lp
+    M, N = 512, 128
+    T = torch.rand((M, N, 4), device="cuda")
+    lf = api.LightField(T, "f32")
+    views = [lf_inputs.look_at((2.4, 0.3, 0.4), (0, 0, 0), 32, 32)]
+    _, idx = lf.render(views, with_idx=True)
+    g = torch.ones((32 * 32, 4), device="cuda")
+    bad = idx.clone()
+    hit = torch.nonzero(bad[:, 0] >= 0)[0, 0]
+    bad[hit, 1] = M + 7                       # out of range: skipped and reported, never read
+    lf.render_backward(views, g, idx=bad)
+    with pytest.raises(lp.LfError) as e:
+        lf.sync_status()
+    assert e.value.status == lp.LF_ERR_DEVICE_CHECK
+    lf.sync_status()                          # the word was cleared
+    with pytest.raises(ValueError):
+        lf.render_backward(views, g, idx=idx[: 10])
+    lf.close()
