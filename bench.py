@@ -453,67 +453,68 @@ def run_precompute(args):
 
 def run_fit_steps(args):
     """Differentiation workload: 16,384 x 512 RGB FP32 table, 32 target views of
-    512x512; one step = render (forward kernel, writing its sample indices) + MSE
-    + backward scatter kernel from those indices + Adam on the FP32 table. Times
-    the steps and the backward launches alone, and once more the backward that
-    searches the indices again (lf_render_backward)."""
+    512x512 per rank (weak scaling: rank r fits views 32r .. 32r+31 of one
+    seeded pool); one step = render (forward kernel, writing its sample indices)
+    + MSE + backward scatter kernel from those indices + one all-reduce of the
+    gradient table over the ranks + Adam on the FP32 table (torch_api.fit_step).
+    Times the steps and the backward launches alone, and once more the backward
+    that searches the indices again (lf_render_backward)."""
     import torch
+    from paper_1903_03837_gb300 import replicas
     from paper_1903_03837_gb300 import torch_api as api
-    cfg = lf_inputs.config_differentiation()
-    train = lf_inputs.pack_offsets(cfg.views[:cfg.extra["n_train"]])
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    rank = dist.get_rank() if world > 1 else 0
+    base = lf_inputs.config_differentiation()
+    n_train = base.extra["n_train"]
+    cfg = lf_inputs.config_differentiation(n_train=n_train * world)
+    train = lf_inputs.pack_offsets(replicas.shard(cfg.views[:n_train * world], rank, world))
     rays = lf_inputs.total_pixels(train)
     gt = api.fill_lobe_table(cfg.lobes(), cfg.M, cfg.N)
     lf_gt = api.LightField(gt, "f32", borrow=True)
     target, _ = lf_gt.render(train)
     table = torch.zeros_like(gt, requires_grad=True)
+    table.grad = torch.zeros_like(table)
     lf = api.LightField(table.detach(), "f32", borrow=True)
     opt = torch.optim.Adam([table], lr=cfg.extra["lr"])
     st = torch.cuda.current_stream()
-    bwd_ms = []
     idx = torch.empty((rays, 2 * lf.K), dtype=torch.int32, device="cuda")
-
-    def step(timed):
-        opt.zero_grad(set_to_none=False)
-        img, _ = lf.render(train, idx=idx)
-        g = (2.0 / img.numel()) * (img - target)
-        if timed:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(st)
-        lf.render_backward(train, g, table.grad, idx=idx)
-        if timed:
-            b.record(st)
-            bwd_ms.append((a, b))
-        opt.step()
+    global_values = rays * world * cfg.C
     for _ in range(args.warmup):
-        step(False)
+        api.fit_step(lf, table, opt, train, target, idx, global_values)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
-        step(True)
+        api.fit_step(lf, table, opt, train, target, idx, global_values)
     e1.record(st)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    bms = sum(a.elapsed_time(b) for a, b in bwd_ms) / len(bwd_ms)
-    # the backward that searches again, for comparison (same gradient buffer, same frame)
-    g = (2.0 / target.numel()) * (lf.render(train)[0] - target)
-    for _ in range(2):
-        lf.render_backward(train, g, table.grad)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
-    for _ in range(5):
-        lf.render_backward(train, g, table.grad)
-    b.record(st)
-    torch.cuda.synchronize()
-    bms_search = a.elapsed_time(b) / 5
+    ms = replicas.reduce_max(e0.elapsed_time(e1) / args.steps)
+    # the backward alone: from the forward's indices, and searching again
+    g = (2.0 / global_values) * (lf.render(train, idx=idx)[0] - target)
+    res = {}
+    for name, kw in (("backward_ms", {"idx": idx}), ("backward_search_ms", {})):
+        for _ in range(2):
+            lf.render_backward(train, g, table.grad, **kw)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(5):
+            lf.render_backward(train, g, table.grad, **kw)
+        b.record(st)
+        torch.cuda.synchronize()
+        res[name] = replicas.reduce_max(a.elapsed_time(b) / 5)
     lf.close()
     lf_gt.close()
+    bms = res["backward_ms"]
     return {"workload": f"differentiation: {cfg.M:,} x {cfg.N:,} RGB FP32 table, {len(train)} views 512x512 "
-                        f"({rays:,} rays), Adam lr 1e-2",
+                        f"per rank ({rays:,} rays per rank), Adam lr 1e-2, gradient all-reduce over "
+                        f"{world} rank(s)",
             "ms_per_fit_step": ms, "fit_steps_per_s": 1e3 / ms,
-            "backward_ms": bms, "backward_grays_s": rays / (bms * 1e-3) / 1e9,
-            "backward_search_ms": bms_search,
-            "fwd_bwd_adam_grays_s": rays / (ms * 1e-3) / 1e9}
+            "backward_ms": bms, "backward_grays_s": world * rays / (bms * 1e-3) / 1e9,
+            "backward_search_ms": res["backward_search_ms"],
+            "fwd_bwd_adam_grays_s": world * rays / (ms * 1e-3) / 1e9}
 
 
 def run_batching(args):
@@ -699,16 +700,19 @@ def main():
             return
         print(json.dumps(run_reference(args, rank, world)), flush=True)
         return
-    if args.workload in ("fit", "precompute"):
-        # profiling cases of the backward and precompute kernels: one JSON object, rank 0 only
-        if rank == 0:
-            leg = run_fit_steps(args) if args.workload == "fit" else run_precompute(args)
-            print(json.dumps({args.workload: leg}), flush=True)
-        return
     if world > 1:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
+    if args.workload in ("fit", "precompute"):
+        # the fit leg (data-parallel over the ranks) or the precompute leg alone
+        # (profiling cases of the backward and precompute kernels): one JSON object
+        leg = run_fit_steps(args) if args.workload == "fit" else run_precompute(args)
+        if rank == 0:
+            print(json.dumps({args.workload: leg}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     line = run_ours(args, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)

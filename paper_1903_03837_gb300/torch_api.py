@@ -162,6 +162,24 @@ def render(table: torch.Tensor, lf: LightField, views) -> torch.Tensor:
     return RenderFunction.apply(table, lf, views)
 
 
+def fit_step(lf, table: torch.Tensor, opt, views, target: torch.Tensor, idx: torch.Tensor,
+             global_values: int) -> torch.Tensor:
+    """One data-parallel fitting step of an FP32 table against target images:
+    render this rank's views (keeping their sample indices), the gradient of
+    the mean squared error over all ranks' `global_values` image values, the
+    backward scatter from those indices into table.grad, one all-reduce of the
+    gradient table, the optimiser step. Returns this rank's sum of squared
+    errors (a 0-d tensor, not synchronised)."""
+    from . import replicas
+    opt.zero_grad(set_to_none=False)
+    img, _ = lf.render(views, idx=idx)
+    diff = img - target
+    lf.render_backward(views, (2.0 / global_values) * diff, table.grad, idx=idx)
+    replicas.allreduce_sum_(table.grad)
+    opt.step()
+    return (diff * diff).sum()
+
+
 def fill_lobe_table(lobes, M: int, N: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """FP32 [M,N,C] lobe radiance field on the GPU (parameters from lf_inputs.draw_lobes)."""
     if out is None:
