@@ -67,23 +67,42 @@ def csrc_digest() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(dtype: str):
-    """DRAM bytes (read + write) per launch of the render kernel on this workload,
-    from the ncu launch list summarised in profiles/render_traffic.txt; None when
-    the kernel sources have changed since that capture."""
+def _recorded():
+    """The per-launch counters of the render kernel on this workload from the ncu
+    launch list summarised in profiles/render_traffic.txt; {} when the kernel
+    sources have changed since that capture."""
     p = os.path.join(ROOT, "profiles", "render_traffic.txt")
     if not os.path.exists(p):
-        return None
+        return {}
     rec = {}
     with open(p) as f:
         for ln in f:
             parts = ln.split()
             if len(parts) == 2 and not ln.startswith("#"):
                 rec[parts[0]] = parts[1]
-    if rec.get("csrc_sha256") != csrc_digest():
-        return None
-    v = rec.get(f"{dtype}_dram_bytes_per_launch")
+    return rec if rec.get("csrc_sha256") == csrc_digest() else {}
+
+
+def recorded_traffic(dtype: str):
+    """DRAM bytes (read + write) per launch, or None (see _recorded)."""
+    v = _recorded().get(f"{dtype}_dram_bytes_per_launch")
     return int(v) if v else None
+
+
+def issue_roofline(dtype: str, launch_s: float):
+    """The render kernel against the SM issue rate (it is issue-bound): thread
+    instructions per launch (recorded by ncu) / the live launch time, against
+    SMs x 4 schedulers x 32 lanes x the maximum SM clock; None without a record."""
+    v = _recorded().get(f"{dtype}_thread_inst_per_launch")
+    if not v:
+        return None
+    from paper_1903_03837_gb300 import lumipath as lp
+    sms, mhz = lp.lf_device_sm_count(), sm_max_mhz()
+    peak = sms * 4 * 32 * mhz * 1e6 / 1e12
+    achieved = int(v) / launch_s / 1e12
+    return {"achieved": achieved, "peak": peak, "unit": "T thread-instructions/s", "frac": achieved / peak,
+            "thread_inst_per_launch": int(v),
+            "peak_source": f"derived: {sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz"}
 
 
 def host_cores() -> int:
@@ -353,7 +372,8 @@ def run_ours(args, rank: int, world: int):
                      "frac": achieved / peak, "traffic": recorded_traffic(args.dtype),
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "kernel": f"lfk::render_kernel<{args.dtype}>", "avg_launch_ms": avg_launch_s * 1e3},
+                     "kernel": f"lfk::render_kernel<{args.dtype}>", "avg_launch_ms": avg_launch_s * 1e3,
+                     "issue": issue_roofline(args.dtype, avg_launch_s)},
         "clocks": clocks,
         "e2e": {"value": world * args.steps * rays / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * 72, "d2h_bytes_per_step": rays * 16,

@@ -30,6 +30,10 @@ lf_status fail(lf_status s, const char *fmt, ...)
     return s;
 }
 
+// Vector loads, stores and atomics need their natural alignment; a misaligned
+// caller pointer is an argument error, never a device fault.
+bool misaligned(const void *p, uintptr_t a) { return p && ((uintptr_t)p & (a - 1)); }
+
 lf_status cuda_fail(cudaError_t e, const char *what)
 {
     if (e == cudaErrorMemoryAllocation) {
@@ -153,6 +157,11 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
 {
     lf_status s = check_views(views, n_views);
     if (s != LF_OK) return s;
+    const uintptr_t va = t->C == 4 ? 16 : 4;      // float4 image / gradient accesses for 4 channels
+    if (misaligned(out, va) || misaligned(grad_out, va) || misaligned(grad, va))
+        return fail(LF_ERR_INVALID_ARG, "image and gradient buffers must be %u-byte aligned", (unsigned)va);
+    if (misaligned(idx, 8)) return fail(LF_ERR_INVALID_ARG, "idx must be 8-byte aligned");
+    if (misaligned(idx_in, 4)) return fail(LF_ERR_INVALID_ARG, "idx must be 4-byte aligned");
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != t->device) return fail(LF_ERR_INVALID_ARG, "table lives on device %d, current is %d", t->device, dev);
@@ -283,6 +292,13 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
     const bool borrow = (d->flags & LF_TABLE_BORROW) != 0;
     if (borrow && quant && C != 4)
         return fail(LF_ERR_INVALID_ARG, "a borrowed F16/E4M3 table must have 4 channels");
+    if (borrow) {
+        // texel loads: float4 (F32, 4 channels), float2 + float (F32, 3), uint2 (F16), uint32 (E4M3)
+        const uintptr_t a = !quant ? (C == 4 ? 16 : 8) : (d->dtype == LF_DTYPE_F16 ? 8 : 4);
+        if (misaligned(radiance_dev, a))
+            return fail(LF_ERR_INVALID_ARG, "a borrowed table must be %u-byte aligned", (unsigned)a);
+        if (misaligned(row_scales_dev, 4)) return fail(LF_ERR_INVALID_ARG, "row scales must be 4-byte aligned");
+    }
     const uint64_t texels = (uint64_t)rows * N;
     if (texels > (1ull << 40)) return fail(LF_ERR_INVALID_ARG, "table too large");
 

@@ -862,10 +862,16 @@ __device__ __forceinline__ float4 texel_f32x4(const void *base, size_t t)
 {
     return __ldg(reinterpret_cast<const float4 *>(base) + t);
 }
+// 12-byte texels in two loads: the texel's 8-byte-aligned pair (its first two
+// floats for even t, its last two for odd t; the table is 8-byte aligned) and
+// the remaining float.
 __device__ __forceinline__ float4 texel_f32x3(const void *base, size_t t)
 {
     const float *p = reinterpret_cast<const float *>(base) + 3 * t;
-    return make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), 0.0f);
+    const bool odd = (t & 1) != 0;
+    const float2 pair = __ldg(reinterpret_cast<const float2 *>(p + (odd ? 1 : 0)));
+    const float one = __ldg(p + (odd ? 0 : 2));
+    return odd ? make_float4(one, pair.x, pair.y, 0.0f) : make_float4(pair.x, pair.y, one, 0.0f);
 }
 __device__ __forceinline__ float4 texel_f16x4(const void *base, size_t t)
 {

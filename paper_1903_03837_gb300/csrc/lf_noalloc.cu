@@ -148,6 +148,14 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
         return na_fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
     if ((d->flags & LF_TABLE_UPPER_HEMISPHERE) && M < 2)
         return na_fail(LF_ERR_INVALID_ARG, "an upper-hemisphere table needs M >= 2");
+    {
+        // natural alignment of the vector accesses (a misaligned pointer is an argument error)
+        const uintptr_t ta = !quant ? (C == 4 ? 16 : 8) : (d->dtype == LF_DTYPE_F16 ? 8 : 4);
+        const uintptr_t oa = C == 4 ? 16 : 4;
+        if (((uintptr_t)radiance_dev & (ta - 1)) || ((uintptr_t)out_dev & (oa - 1)) ||
+            ((uintptr_t)idx_dev & 7u) || ((uintptr_t)row_scales_dev & 3u))
+            return na_fail(LF_ERR_INVALID_ARG, "misaligned table, scale, image or index buffer");
+    }
     if (n_views == 0 || n_views > 65536) return na_fail(LF_ERR_INVALID_ARG, "n_views must be in [1, 65536]");
     for (uint32_t v = 0; v < n_views; ++v) {
         const lf_view &w = views[v];

@@ -173,3 +173,15 @@ def test_precompute_null_and_misaligned_arguments():
     assert L.lf_precompute_table(C.byref(d), None, C.c_void_p(4096), None) == lp.LF_ERR_INVALID_ARG
     assert L.lf_precompute_table(C.byref(d), _blobs(), C.c_void_p(4100), None) == lp.LF_ERR_INVALID_ARG
     assert "aligned" in lp.lf_last_error()
+
+
+@pytest.mark.parametrize("dtype,Cc,ptr", [(0, 4, 0x1008), (0, 3, 0x1004), (1, 4, 0x1004), (2, 4, 0x1002)])
+def test_borrowed_table_must_be_aligned_for_its_vector_loads(dtype, Cc, ptr):
+    # float4 (F32 RGBA), float2 + float (F32 RGB), uint2 (F16), uint32 (E4M3) texel loads:
+    # a misaligned pointer is an argument error before any device work
+    d = _desc(C=Cc, dtype=dtype, flags=lp.LF_TABLE_BORROW)
+    handle = C.c_void_p()
+    s = lp.lib().lf_create_table(C.byref(d), C.c_void_p(ptr), C.c_void_p(0x2000), None, C.byref(handle))
+    assert s == lp.LF_ERR_INVALID_ARG, lp.lf_last_error()
+    assert "aligned" in lp.lf_last_error()
+    assert handle.value is None

@@ -476,3 +476,31 @@ def test_backward_from_indices_rejects_bad_indices(api):
     with pytest.raises(ValueError):
         lf.render_backward(views, g, idx=idx[: 10])
     lf.close()
+
+
+def test_misaligned_buffers_are_argument_errors(api):
+    """Vector stores and loads need aligned buffers: a misaligned image, index or
+    gradient buffer is rejected on the host (LF_ERR_INVALID_ARG), never launched."""
+    from paper_1903_03837_gb300 import lumipath as lp
+    T = torch.rand((256, 64, 4), device="cuda")
+    lf = api.LightField(T, "f32")
+    views = [lf_inputs.look_at((2.4, 0.3, 0.4), (0, 0, 0), 16, 16)]
+    P = 256
+    out_bad = torch.empty(P * 4 + 1, device="cuda")[1:]          # 4 bytes off a 16-byte boundary
+    idx_bad = torch.empty(P * 10 + 1, dtype=torch.int32, device="cuda")[1:]
+    g = torch.ones((P, 4), device="cuda")
+    grad_bad = torch.zeros(256 * 64 * 4 + 1, device="cuda")[1:]
+    with pytest.raises(lp.LfError) as e:
+        lf.render(views, out=out_bad)
+    assert e.value.status == lp.LF_ERR_INVALID_ARG
+    with pytest.raises(lp.LfError) as e:
+        lf.render(views, idx=idx_bad)
+    assert e.value.status == lp.LF_ERR_INVALID_ARG
+    with pytest.raises(lp.LfError) as e:
+        lf.render_backward(views, g, grad_bad.view(256, 64, 4))
+    assert e.value.status == lp.LF_ERR_INVALID_ARG
+    lf.sync_status()                                              # nothing ran, nothing recorded
+    out, _ = lf.render(views)                                     # aligned buffers still work
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    lf.close()
