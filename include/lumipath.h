@@ -139,6 +139,14 @@ lf_status lf_create_table(const lf_table_desc *desc, const void *radiance_dev,
 lf_status lf_render(const lf_table *t, const lf_view *views_host, uint32_t n_views,
                     float *out_dev, int32_t *idx_dev, void *stream);
 
+/* lf_render with the image stored as IEEE binary16 (out_dev: device uint16
+ * [P][C], each value the FP32 result of lf_render rounded once to nearest
+ * even): half the bytes for a caller that reads the image back to the host.
+ * Alignment: 8 bytes for C = 4, 2 for C = 3. Errors as lf_render, and
+ * LF_ERR_UNSUPPORTED for a table with k_nearest = 9. */
+lf_status lf_render_f16(const lf_table *t, const lf_view *views_host, uint32_t n_views,
+                        uint16_t *out_dev, int32_t *idx_dev, void *stream);
+
 /* Gradient of the render with respect to the table: for every hit ray and
  * every tap (a, b), grad_table[i_a][j_b][c] += W_ab * grad_out[ray][c]
  * (the adjoint of the linear blend). grad_out_dev: device FP32 [P][C];

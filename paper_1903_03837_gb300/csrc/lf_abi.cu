@@ -153,12 +153,14 @@ lf_status run_chunk(const lf_table *t, const lfk::RenderParamsBase &base, const 
 }
 
 lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *out, int32_t *idx,
-              const float *grad_out, float *grad, void *stream, const int32_t *idx_in = nullptr)
+              const float *grad_out, float *grad, void *stream, const int32_t *idx_in = nullptr,
+              bool out_f16 = false)
 {
     lf_status s = check_views(views, n_views);
     if (s != LF_OK) return s;
     const uintptr_t va = t->C == 4 ? 16 : 4;      // float4 image / gradient accesses for 4 channels
-    if (misaligned(out, va) || misaligned(grad_out, va) || misaligned(grad, va))
+    const uintptr_t oa = out_f16 ? (t->C == 4 ? 8 : 2) : va;
+    if (misaligned(out, oa) || misaligned(grad_out, va) || misaligned(grad, va))
         return fail(LF_ERR_INVALID_ARG, "image and gradient buffers must be %u-byte aligned", (unsigned)va);
     if (misaligned(idx, 8)) return fail(LF_ERR_INVALID_ARG, "idx must be 8-byte aligned");
     if (misaligned(idx_in, 4)) return fail(LF_ERR_INVALID_ARG, "idx must be 4-byte aligned");
@@ -177,6 +179,7 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
     b.out = out;
     b.idx = idx;
     b.idx_in = idx_in;
+    b.out_f16 = out_f16 ? 1u : 0u;
     b.grad_out = grad_out;
     b.grad = grad;
     b.status = t->scratch;
@@ -402,6 +405,17 @@ lf_status lf_render(const lf_table *t, const lf_view *views, uint32_t n_views, f
     if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
     if (!out_dev) return fail(LF_ERR_INVALID_ARG, "out is NULL");
     return run(t, views, n_views, out_dev, idx_dev, nullptr, nullptr, stream);
+}
+
+lf_status lf_render_f16(const lf_table *t, const lf_view *views, uint32_t n_views, uint16_t *out_dev,
+                        int32_t *idx_dev, void *stream)
+{
+    g_err.clear();
+    if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
+    if (!out_dev) return fail(LF_ERR_INVALID_ARG, "out is NULL");
+    if (t->desc.k_nearest == 9) return fail(LF_ERR_UNSUPPORTED, "a binary16 image with 9 neighbours is not built");
+    return run(t, views, n_views, reinterpret_cast<float *>(out_dev), idx_dev, nullptr, nullptr, stream, nullptr,
+               true);
 }
 
 lf_status lf_render_backward(const lf_table *t, const lf_view *views, uint32_t n_views,

@@ -20,7 +20,8 @@ struct RenderParamsBase {
     const float *scales;           // [M] (F16 / E4M3)
     uint32_t N;                    // texels per origin row
     uint32_t C;                    // output / gradient channels (3 or 4)
-    float *out;                    // forward: [P][C]
+    float *out;                    // forward: [P][C] FP32, or binary16 when out_f16
+    uint32_t out_f16;              // 1: the image is stored as binary16 (round to nearest even)
     int32_t *idx;                  // forward: [P][2K] or NULL
     const int32_t *idx_in;         // backward: the forward's [P][2K] indices, or NULL (search again)
     const float *grad_out;         // backward: [P][C]

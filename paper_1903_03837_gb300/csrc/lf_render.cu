@@ -9,6 +9,7 @@
 // of SMs x occupancy CTAs; the last CTA to leave resets the queue, so the
 // launch is replayable, e.g. from a CUDA graph). Views live in the kernel's
 // parameter space (no device copy, graph friendly).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lf_device.cuh"
@@ -189,6 +190,23 @@ __device__ __forceinline__ bool samples_from_idx(const RenderParamsBase &p, cons
     return true;
 }
 
+// binary16 image: the FP32 result rounded once (half the bytes to read back).
+__device__ __forceinline__ void store_f16(float *out, uint32_t C, uint64_t pix, float4 acc)
+{
+    const __half2 xy = __floats2half2_rn(acc.x, acc.y), zw = __floats2half2_rn(acc.z, acc.w);
+    if (C == 4) {
+        uint2 v;
+        v.x = *reinterpret_cast<const uint32_t *>(&xy);
+        v.y = *reinterpret_cast<const uint32_t *>(&zw);
+        __stcs(reinterpret_cast<uint2 *>(out) + pix, v);
+    } else {
+        unsigned short *o = reinterpret_cast<unsigned short *>(out) + pix * 3;
+        __stcs(o, __half_as_ushort(__low2half(xy)));
+        __stcs(o + 1, __half_as_ushort(__high2half(xy)));
+        __stcs(o + 2, __half_as_ushort(__low2half(zw)));
+    }
+}
+
 // Packed FP32 pair FMA (one instruction for two lanes of a texel).
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
 {
@@ -200,7 +218,7 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
     return *reinterpret_cast<float2 *>(&rd);
 }
 
-template <int DT, int K>
+template <int DT, int K, bool F16>
 __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const ViewK &v, uint32_t px,
                                            uint32_t py)
 {
@@ -256,7 +274,9 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
     }
     const float4 acc = make_float4(acc_xy.x, acc_xy.y, acc_zw.x, acc_zw.y);
     uint64_t pix = v.out_offset + (uint64_t)py * v.width + px;
-    if (p.C == 4) {
+    if constexpr (F16) {
+        store_f16(p.out, p.C, pix, acc);
+    } else if (p.C == 4) {
         __stcs(reinterpret_cast<float4 *>(p.out) + pix, acc);
     } else {
         float *o = p.out + pix * 3;
@@ -400,7 +420,7 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
 }
 
 
-template <int DT, int MAXV, bool BWD, int K>
+template <int DT, int MAXV, bool BWD, int K, bool F16 = false>
 __global__ void __launch_bounds__(kMaxBlock, K == 5 ? LF_MIN_BLOCKS : 2)
     render_kernel(const __grid_constant__ RenderParams<MAXV> p)
 {
@@ -427,7 +447,7 @@ __global__ void __launch_bounds__(kMaxBlock, K == 5 ? LF_MIN_BLOCKS : 2)
         if constexpr (BWD) {
             backward_ray<K>(p, &vw, active, px, py);
         } else {
-            if (active) render_ray<DT, K>(p, vw, px, py);
+            if (active) render_ray<DT, K, F16>(p, vw, px, py);
         }
         if (!p.persistent) break;
         __syncthreads();               // everyone has read s_tile before it is rewritten
@@ -442,7 +462,7 @@ __global__ void __launch_bounds__(kMaxBlock, K == 5 ? LF_MIN_BLOCKS : 2)
     }
 }
 
-template <int MAXV, int K>
+template <int MAXV, int K, bool F16>
 static cudaError_t launch_k(int kind, bool bwd, const RenderParams<MAXV> &p, unsigned grid, unsigned block,
                             cudaStream_t st)
 {
@@ -450,33 +470,36 @@ static cudaError_t launch_k(int kind, bool bwd, const RenderParams<MAXV> &p, uns
         render_kernel<kF32C4, MAXV, true, K><<<grid, block, 0, st>>>(p);
     } else {
         switch (kind) {
-        case kF32C4: render_kernel<kF32C4, MAXV, false, K><<<grid, block, 0, st>>>(p); break;
-        case kF32C3: render_kernel<kF32C3, MAXV, false, K><<<grid, block, 0, st>>>(p); break;
-        case kF16C4: render_kernel<kF16C4, MAXV, false, K><<<grid, block, 0, st>>>(p); break;
-        default: render_kernel<kE4M3C4, MAXV, false, K><<<grid, block, 0, st>>>(p); break;
+        case kF32C4: render_kernel<kF32C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p); break;
+        case kF32C3: render_kernel<kF32C3, MAXV, false, K, F16><<<grid, block, 0, st>>>(p); break;
+        case kF16C4: render_kernel<kF16C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p); break;
+        default: render_kernel<kE4M3C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p); break;
         }
     }
     return cudaGetLastError();
 }
 
+// Five neighbours: FP32 or binary16 image; nine neighbours: FP32 image (the
+// host refuses a binary16 image with nine).
 template <int MAXV>
 static cudaError_t launch_t(int kind, bool bwd, const RenderParams<MAXV> &p, unsigned grid,
                             unsigned block, cudaStream_t st)
 {
-    return p.nine ? launch_k<MAXV, 9>(kind, bwd, p, grid, block, st)
-                  : launch_k<MAXV, 5>(kind, bwd, p, grid, block, st);
+    if (p.nine) return launch_k<MAXV, 9, false>(kind, bwd, p, grid, block, st);
+    return p.out_f16 && !bwd ? launch_k<MAXV, 5, true>(kind, bwd, p, grid, block, st)
+                             : launch_k<MAXV, 5, false>(kind, bwd, p, grid, block, st);
 }
 
-template <int MAXV, int K>
+template <int MAXV, int K, bool F16>
 static int occupancy_k(int kind, bool bwd, unsigned block)
 {
     int n = 0;
     const void *f;
     if (bwd) f = (const void *)render_kernel<kF32C4, MAXV, true, K>;
-    else if (kind == kF32C4) f = (const void *)render_kernel<kF32C4, MAXV, false, K>;
-    else if (kind == kF32C3) f = (const void *)render_kernel<kF32C3, MAXV, false, K>;
-    else if (kind == kF16C4) f = (const void *)render_kernel<kF16C4, MAXV, false, K>;
-    else f = (const void *)render_kernel<kE4M3C4, MAXV, false, K>;
+    else if (kind == kF32C4) f = (const void *)render_kernel<kF32C4, MAXV, false, K, F16>;
+    else if (kind == kF32C3) f = (const void *)render_kernel<kF32C3, MAXV, false, K, F16>;
+    else if (kind == kF16C4) f = (const void *)render_kernel<kF16C4, MAXV, false, K, F16>;
+    else f = (const void *)render_kernel<kE4M3C4, MAXV, false, K, F16>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, (int)block, 0) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
 }
@@ -494,8 +517,10 @@ cudaError_t launch_render_large(int kind, bool bwd, const RenderParams<kLargeVie
 int render_occupancy(int kind, bool bwd, bool large, bool nine, unsigned block)
 {
     if (nine)
-        return large ? occupancy_k<kLargeViews, 9>(kind, bwd, block) : occupancy_k<kSmallViews, 9>(kind, bwd, block);
-    return large ? occupancy_k<kLargeViews, 5>(kind, bwd, block) : occupancy_k<kSmallViews, 5>(kind, bwd, block);
+        return large ? occupancy_k<kLargeViews, 9, false>(kind, bwd, block)
+                     : occupancy_k<kSmallViews, 9, false>(kind, bwd, block);
+    return large ? occupancy_k<kLargeViews, 5, false>(kind, bwd, block)
+                 : occupancy_k<kSmallViews, 5, false>(kind, bwd, block);
 }
 
 }  // namespace lfk

@@ -83,6 +83,7 @@ def lib():
             sig = {
                 "lf_create_table": (st, [C.POINTER(lf_table_desc), vp, vp, vp, C.POINTER(vp)]),
                 "lf_render": (st, [vp, C.POINTER(lf_view), u32, vp, vp, vp]),
+                "lf_render_f16": (st, [vp, C.POINTER(lf_view), u32, vp, vp, vp]),
                 "lf_render_backward": (st, [vp, C.POINTER(lf_view), u32, vp, vp, vp]),
                 "lf_render_backward_idx": (st, [vp, C.POINTER(lf_view), u32, vp, vp, vp, vp]),
                 "lf_destroy": (None, [vp]),
@@ -148,6 +149,11 @@ def lf_create_table(desc: lf_table_desc, radiance_ptr: int, scales_ptr: Optional
 def lf_render(table: int, views, n_views: int, out_ptr: int, idx_ptr: Optional[int], stream: int = 0):
     _check(lib().lf_render(C.c_void_p(table), views, n_views, C.c_void_p(out_ptr),
                            C.c_void_p(idx_ptr or None), C.c_void_p(stream or None)))
+
+
+def lf_render_f16(table: int, views, n_views: int, out_ptr: int, idx_ptr: Optional[int], stream: int = 0):
+    _check(lib().lf_render_f16(C.c_void_p(table), views, n_views, C.c_void_p(out_ptr),
+                               C.c_void_p(idx_ptr or None), C.c_void_p(stream or None)))
 
 
 def lf_render_backward(table: int, views, n_views: int, grad_out_ptr: int, grad_table_ptr: int,

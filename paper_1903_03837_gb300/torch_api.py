@@ -79,13 +79,17 @@ class LightField:
 
     # -- rendering -------------------------------------------------------------
     def render(self, views: Sequence, out: Optional[torch.Tensor] = None, with_idx: bool = False,
-               idx: Optional[torch.Tensor] = None) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+               idx: Optional[torch.Tensor] = None,
+               half: bool = False) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+        """Render `views` into out [P, C] (float32, or float16 with half=True:
+        the FP32 result rounded once, lf_render_f16)."""
         P = total_pixels(views)
+        odt = torch.float16 if half else torch.float32
         if out is None:
-            out = torch.empty((P, self.C), dtype=torch.float32, device="cuda")
+            out = torch.empty((P, self.C), dtype=odt, device="cuda")
         _need_cuda(out, "out")
-        if out.numel() < P * self.C or out.dtype != torch.float32:
-            raise ValueError("out must be float32 with at least P*C elements")
+        if out.numel() < P * self.C or out.dtype != odt:
+            raise ValueError(f"out must be {odt} with at least P*C elements")
         if with_idx and idx is None:
             idx = torch.empty((P, 2 * self.K), dtype=torch.int32, device="cuda")
         if idx is not None:
@@ -93,8 +97,8 @@ class LightField:
             if idx.numel() < P * 2 * self.K or idx.dtype != torch.int32:
                 raise ValueError("idx must be int32 with at least P*2K elements")
         vv = lp.make_views(views)
-        lp.lf_render(self.handle, vv, len(views), out.data_ptr(), idx.data_ptr() if idx is not None else None,
-                     _stream())
+        fn = lp.lf_render_f16 if half else lp.lf_render
+        fn(self.handle, vv, len(views), out.data_ptr(), idx.data_ptr() if idx is not None else None, _stream())
         return out, idx
 
     def render_backward(self, views: Sequence, grad_out: torch.Tensor,

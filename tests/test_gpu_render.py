@@ -504,3 +504,26 @@ def test_misaligned_buffers_are_argument_errors(api):
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()
     lf.close()
+
+
+@pytest.mark.parametrize("dtype,Cc", [("e4m3", 4), ("f32", 3), ("f32", 4)])
+def test_binary16_image_is_the_rounded_fp32_image(api, dtype, Cc):
+    """lf_render_f16: the same render, each value rounded once to binary16 (RNE)."""
+    M, N = 2048, 256
+    rng = np.random.default_rng(Cc)
+    T = rng.uniform(0, 2, (M, N, Cc)).astype(np.float32)
+    if dtype == "e4m3":
+        codes, scales = oracle.quantize_rows(T, "e4m3")
+        lf = api.LightField(torch.from_numpy(codes).cuda(), "e4m3", torch.from_numpy(scales).cuda())
+    else:
+        lf = api.LightField(torch.from_numpy(T).cuda(), "f32")
+    views = lf_inputs.pack_offsets([lf_inputs.look_at((2.4, 0.3, 0.4), (0, 0, 0), 96, 80),
+                                    lf_inputs.look_at((0.1, 0.05, 2.6), (0, 0, 0), 33, 17)])
+    out32, idx32 = lf.render(views, with_idx=True)
+    out16, idx16 = lf.render(views, with_idx=True, half=True)
+    lf.sync_status()
+    assert out16.dtype == torch.float16
+    assert torch.equal(idx16, idx32)
+    assert torch.equal(out16, out32.half())          # torch's conversion rounds to nearest even
+    assert (out16 != 0).any()
+    lf.close()
