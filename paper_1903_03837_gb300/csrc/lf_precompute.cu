@@ -9,7 +9,8 @@
 // b at step k (t_k = (k + 1/2) dt) is
 //   exp2(la_b - y_k^2),  la_b = log2(kappa_b) - a_b^2 |f_b x d|^2,
 //                        y_k  = a_b (f_b . d + 1/2 dt) + k (a_b dt),
-// two fma and one ex2 per blob-step. The cross product keeps the distance of
+// two fma and one ex2 per blob-step (with blobs taken in pairs: one packed
+// fma, mul and sub per pair and two ex2). The cross product keeps the distance of
 // the ray from a narrow blob's centre accurate (|f|^2 - (f.d)^2 would cancel).
 // The emission is accumulated per blob, G_b += w_k g_bk with w_k the step's
 // compositing weight, and turned into colour once per sample: sum_b G_b emit_b
@@ -33,6 +34,34 @@ __device__ __forceinline__ float ex2_approx(float x)
     return r;
 }
 
+// Packed FP32 pairs (one instruction for two blobs).
+__device__ __forceinline__ unsigned long long pk(float2 a) { return *reinterpret_cast<unsigned long long *>(&a); }
+__device__ __forceinline__ float2 upk(unsigned long long r) { return *reinterpret_cast<float2 *>(&r); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+
 // (1 - exp(-x)) / x for x >= 0, given E = exp(-x): the Taylor series of the
 // left side below x = 1/16 (truncation < x^5/720 < 2^-29 relative), the
 // quotient above (cancellation in 1 - E costs at most 16 ulp there). Both are
@@ -45,13 +74,18 @@ __device__ __forceinline__ float one_minus_exp_over_x(float x, float E)
 }
 
 // CTAs of 256 threads per SM the register budget of the 8-blob kernel is cut
-// for, and the unroll of the step loop (both measured: 2 and 4 were fastest).
+// for, and the unroll of the step loop (measured with the packed blob loop:
+// 2 CTAs and 2 steps were fastest).
 #ifndef LF_PRE_MIN_BLOCKS
 #define LF_PRE_MIN_BLOCKS 2
 #endif
 
+// 1: the blob loop in packed FP32 pairs (fma/mul/sub/add .f32x2); 0: scalar.
+#ifndef LF_PRE_PACKED
+#define LF_PRE_PACKED 1
+#endif
 #ifndef LF_PRE_STEP_UNROLL
-#define LF_PRE_STEP_UNROLL 4
+#define LF_PRE_STEP_UNROLL 2
 #endif
 constexpr int kPreStepUnroll = LF_PRE_STEP_UNROLL;
 
@@ -133,6 +167,45 @@ __global__ void __launch_bounds__(256, BMAX <= 8 ? LF_PRE_MIN_BLOCKS : 1)
 
             float T = 1.0f;
             if (dt > 0.0f) {
+#if LF_PRE_PACKED
+                // blobs in pairs: y, y^2, the exponent, the density sum and the
+                // per-blob weights in packed FP32 pairs
+                constexpr int BP = BMAX / 2;
+                float2 Y0[BP], DY[BP], LA[BP], G2[BP];
+#pragma unroll
+                for (int q = 0; q < BP; ++q) {
+                    Y0[q] = make_float2(y0[2 * q], y0[2 * q + 1]);
+                    DY[q] = make_float2(dy0[2 * q], dy0[2 * q + 1]);
+                    LA[q] = make_float2(la[2 * q], la[2 * q + 1]);
+                    G2[q] = make_float2(0.0f, 0.0f);
+                }
+                float kf = 0.0f;
+#pragma unroll kPreStepUnroll
+                for (uint32_t st = 0; st < p.steps; ++st, kf += 1.0f) {
+                    const float2 kf2 = make_float2(kf, kf);
+                    float2 g2[BP], sig2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int q = 0; q < BP; ++q) {
+                        const float2 y = fma2(kf2, DY[q], Y0[q]);
+                        const float2 arg = sub2(LA[q], mul2(y, y));
+                        g2[q] = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                        sig2 = add2(sig2, g2[q]);
+                    }
+                    // step of constant density: weight T (1 - e^-x) / sigma = T dt (1 - e^-x) / x
+                    const float xs = (sig2.x + sig2.y) * dt;
+                    const float E = ex2_approx(-xs * kLog2e);
+                    const float w = T * one_minus_exp_over_x(xs, E) * dt;
+                    const float2 w2 = make_float2(w, w);
+#pragma unroll
+                    for (int q = 0; q < BP; ++q) G2[q] = fma2(w2, g2[q], G2[q]);
+                    T *= E;
+                }
+#pragma unroll
+                for (int q = 0; q < BP; ++q) {
+                    G[2 * q] = G2[q].x;
+                    G[2 * q + 1] = G2[q].y;
+                }
+#else
                 float kf = 0.0f;
 #pragma unroll kPreStepUnroll
                 for (uint32_t st = 0; st < p.steps; ++st, kf += 1.0f) {
@@ -151,6 +224,7 @@ __global__ void __launch_bounds__(256, BMAX <= 8 ? LF_PRE_MIN_BLOCKS : 1)
                     for (int k = 0; k < BMAX; ++k) G[k] = fmaf(w, g[k], G[k]);
                     T *= E;
                 }
+#endif
             }
             float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
 #pragma unroll
