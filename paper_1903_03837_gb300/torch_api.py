@@ -1,9 +1,13 @@
 """Tensor-level API over the C ABI: PyTorch supplies device memory and the
 current CUDA stream; the kernels of liblumipath.so do all of the work.
 
-* ``LightField``: a table on the GPU (create / render / backward / launch shape)
+* ``LightField``: a table on the GPU (create / render, FP32 or binary16 image /
+  backward, searching again or from the forward's indices / launch shape)
 * ``RenderFunction``: ``torch.autograd.Function`` whose backward is the
-  library's scatter-add kernel (for fitting a table to target views)
+  library's scatter-add kernel, fed with the forward's indices (for fitting a
+  table to target views); ``fit_step``: one data-parallel fitting step
+* ``precompute_table``: the light-field precompute of Section 3 (rays r_k with
+  jittered origins through an analytic volume), on the GPU
 * ``fill_lobe_table``: the synthetic lobe radiance field, filled on the GPU
 * ``quantize_table``: per-row FP16 / E4M3 storage of an FP32 table
 """
