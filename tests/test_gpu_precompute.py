@@ -127,3 +127,23 @@ def test_repeat_calls_are_deterministic(api):
     vol.seed += 1                       # another jitter stream changes the texels
     c = gpu_table(api, vol, 300, 70, 4)
     assert not np.array_equal(a, c)
+
+
+def test_upper_hemisphere_precompute_renders_like_the_oracle(api):
+    # the paper's storage: only origin rows i < M/2 are precomputed and stored (Section 3)
+    vol = lf_inputs.draw_volume(7, B=6, spp=2, steps=16)
+    M, N = 1024, 256
+    T = api.precompute_table(vol, M, N, 4, rows=M // 2)
+    lf = api.LightField(T, "f32", borrow=True, n_origins=M, upper=True)
+    views = lf_inputs.pack_offsets([lf_inputs.look_at((0.4, -0.3, 2.3), (0, 0, 0), 64, 48),
+                                    lf_inputs.look_at((2.2, 0.5, 0.3), (0, 0, 0), 48, 40)])
+    out, idx = lf.render(views, with_idx=True)
+    lf.sync_status()
+    torch.cuda.synchronize()
+    want_T = oracle.volume_table(vol, M, N, 4, rows=range(M // 2))
+    o_out, o_idx, hits = oracle.render_views(oracle.Scene(M, N, 4, "f32", want_T, upper=True), views)
+    assert hits > 500
+    assert np.array_equal(idx.cpu().numpy(), o_idx)
+    err = np.abs(out.cpu().numpy() - o_out)
+    assert err.max() <= 1e-5 + vol.steps * 2.0 ** -21 * 2.0 + 1e-6, float(err.max())
+    lf.close()
