@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lf_kernels.h"
 #include "lumipath.h"
 
@@ -29,6 +31,13 @@ lf_status fail(lf_status s, const char *fmt, ...)
     g_err = buf;
     return s;
 }
+
+// An NVTX range around one entry point (for nsys/ncu timelines; a no-op when
+// no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Vector loads, stores and atomics need their natural alignment; a misaligned
 // caller pointer is an argument error, never a device fault.
@@ -268,6 +277,7 @@ int lf_device_sm_count(void)
 lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, const float *row_scales_dev,
                           void *stream, lf_table **out)
 {
+    NvtxRange nvtx_("lf_create_table");
     g_err.clear();
     if (!out) return fail(LF_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -401,6 +411,7 @@ lf_status lf_get_launch(const lf_table *t, lf_launch *cfg)
 lf_status lf_render(const lf_table *t, const lf_view *views, uint32_t n_views, float *out_dev,
                     int32_t *idx_dev, void *stream)
 {
+    NvtxRange nvtx_("lf_render");
     g_err.clear();
     if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
     if (!out_dev) return fail(LF_ERR_INVALID_ARG, "out is NULL");
@@ -410,6 +421,7 @@ lf_status lf_render(const lf_table *t, const lf_view *views, uint32_t n_views, f
 lf_status lf_render_f16(const lf_table *t, const lf_view *views, uint32_t n_views, uint16_t *out_dev,
                         int32_t *idx_dev, void *stream)
 {
+    NvtxRange nvtx_("lf_render_f16");
     g_err.clear();
     if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
     if (!out_dev) return fail(LF_ERR_INVALID_ARG, "out is NULL");
@@ -421,6 +433,7 @@ lf_status lf_render_f16(const lf_table *t, const lf_view *views, uint32_t n_view
 lf_status lf_render_backward(const lf_table *t, const lf_view *views, uint32_t n_views,
                              const float *grad_out_dev, float *grad_table_dev, void *stream)
 {
+    NvtxRange nvtx_("lf_render_backward");
     g_err.clear();
     if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
     if (!grad_out_dev || !grad_table_dev) return fail(LF_ERR_INVALID_ARG, "gradient buffer is NULL");
@@ -431,6 +444,7 @@ lf_status lf_render_backward_idx(const lf_table *t, const lf_view *views, uint32
                                  const float *grad_out_dev, const int32_t *idx_dev, float *grad_table_dev,
                                  void *stream)
 {
+    NvtxRange nvtx_("lf_render_backward_idx");
     g_err.clear();
     if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
     if (!grad_out_dev || !grad_table_dev) return fail(LF_ERR_INVALID_ARG, "gradient buffer is NULL");
@@ -456,6 +470,7 @@ lf_status lf_sync_status(lf_table *t, void *stream)
 lf_status lf_quantize_table(const float *src_dev, uint32_t M, uint32_t N, uint32_t C, int32_t dtype,
                             void *codes_dev, float *scales_dev, void *stream)
 {
+    NvtxRange nvtx_("lf_quantize_table");
     g_err.clear();
     if (!src_dev || !codes_dev || !scales_dev) return fail(LF_ERR_INVALID_ARG, "NULL buffer");
     if (M == 0 || N == 0 || M > (1u << 24) || N > (1u << 24)) return fail(LF_ERR_INVALID_ARG, "bad M/N");
@@ -471,6 +486,7 @@ lf_status lf_fill_lobe_table(uint32_t M, uint32_t N, uint32_t C, uint32_t L, con
                              const double *ad, const double *kp, const double *kd, const double *col,
                              uint64_t noise_seed, float *out_dev, void *stream)
 {
+    NvtxRange nvtx_("lf_fill_lobe_table");
     g_err.clear();
     if (!out_dev) return fail(LF_ERR_INVALID_ARG, "out is NULL");
     if (M == 0 || N == 0 || M > (1u << 24) || N > (1u << 24)) return fail(LF_ERR_INVALID_ARG, "bad M/N");
@@ -509,6 +525,7 @@ lf_status lf_fill_lobe_table(uint32_t M, uint32_t N, uint32_t C, uint32_t L, con
 lf_status lf_precompute_table(const lf_precompute_desc *d, const lf_blob *blobs, float *out_dev,
                               void *stream)
 {
+    NvtxRange nvtx_("lf_precompute_table");
     g_err.clear();
     if (!d) return fail(LF_ERR_INVALID_ARG, "desc is NULL");
     if (!out_dev) return fail(LF_ERR_INVALID_ARG, "out is NULL");

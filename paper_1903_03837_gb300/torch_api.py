@@ -188,6 +188,27 @@ def fit_step(lf, table: torch.Tensor, opt, views, target: torch.Tensor, idx: tor
     return (diff * diff).sum()
 
 
+def save_fit_state(path: str, table: torch.Tensor, opt, step: int) -> None:
+    """Checkpoint of a table fit: the FP32 table, the optimiser state and the
+    step, written to `path` atomically (a temporary file, then a rename)."""
+    import os
+    tmp = f"{path}.tmp{os.getpid()}"
+    torch.save({"table": table.detach().cpu(), "opt": opt.state_dict(), "step": int(step)}, tmp)
+    os.replace(tmp, path)
+
+
+def load_fit_state(path: str, table: torch.Tensor, opt) -> int:
+    """Restore a checkpoint of save_fit_state into `table` (in place) and `opt`;
+    returns the step to continue from."""
+    ck = torch.load(path, map_location="cpu", weights_only=True)
+    if tuple(ck["table"].shape) != tuple(table.shape):
+        raise ValueError(f"checkpoint table {tuple(ck['table'].shape)} does not match {tuple(table.shape)}")
+    with torch.no_grad():
+        table.copy_(ck["table"].to(table.device))
+    opt.load_state_dict(ck["opt"])
+    return int(ck["step"])
+
+
 def fill_lobe_table(lobes, M: int, N: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """FP32 [M,N,C] lobe radiance field on the GPU (parameters from lf_inputs.draw_lobes)."""
     if out is None:
