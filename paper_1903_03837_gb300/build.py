@@ -47,13 +47,21 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and not extra_flags and up_to_date():
+DEBUG_DIR = os.path.join(BUILD, "debug")
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str = None) -> str:
+    """Compile every .cu of csrc/ in parallel and link liblumipath.so. With
+    `out_dir` the objects and the library go there instead of _build/ (e.g. the
+    debug build: extra_flags=["-DLF_DEBUG_CHECKS"], out_dir=DEBUG_DIR)."""
+    bdir = out_dir or BUILD
+    lib = os.path.join(bdir, "liblumipath.so")
+    if not force and not extra_flags and out_dir is None and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def comp(pair):
         s, o = pair
@@ -69,12 +77,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for lg in logs:
             if lg.strip():
                 print(lg)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

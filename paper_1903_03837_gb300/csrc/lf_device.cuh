@@ -497,7 +497,7 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
         if (src.w.interior) {
 #pragma unroll
             for (int s = 0; s < kWindow; ++s) {
-                float dd = dist2_hi(P, window_index(src.w, s), qh);
+                float dd = dist2_hi(P, LF_DINDEX(window_index(src.w, s), P.n, status, kStatusDebugPoint), qh);
                 k[s] = (__float_as_uint(dd) & ~15u) | (uint32_t)s;
             }
         } else {
@@ -518,7 +518,8 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
 #pragma unroll
         for (int m = 0; m < 7; ++m) s7[m] = kNone;
         for (int s = 0; s < src.scan_cnt; ++s)
-            insert7(s7, (__float_as_uint(dist2_hi(P, src.scan_base + s, qh)) & ~mask1) | (uint32_t)s);
+            insert7(s7, (__float_as_uint(dist2_hi(P, LF_DINDEX(src.scan_base + s, P.n, status, kStatusDebugPoint), qh)) &
+                         ~mask1) | (uint32_t)s);
     }
 
     // Bounds of the exact squared distance behind each of the 7 keys: the key
@@ -539,7 +540,7 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
     for (int m = 0; m < 5; ++m) {
         bool ok = s7[m] != kNone;
         i5[m] = ok ? source_index(src, (int)(s7[m] & mask1)) : 0;
-        p5[m] = dist2_df(P, i5[m], qh, ql);
+        p5[m] = dist2_df(P, LF_DINDEX(i5[m], P.n, status, kStatusDebugPoint), qh, ql);
     }
     // Order certificate at tier 1: each of the top 6 lies strictly below the
     // next by more than any FP64 rounding of the ranking distances (2^-40), so

@@ -8,6 +8,24 @@
 
 namespace lfk {
 
+// Bits of a table's device status word (read back by lf_sync_status).
+constexpr uint32_t kStatusIndex = 1u;        // a search returned an index out of range (recorded, replaced by 0)
+constexpr uint32_t kStatusIdxInput = 2u;     // given indices disagree with the ray (backward from indices)
+constexpr uint32_t kStatusDebugPoint = 4u;   // debug build: a point index about to be read is out of range
+constexpr uint32_t kStatusDebugTexel = 8u;   // debug build: a texel index about to be read is out of range
+constexpr uint32_t kStatusDebugGrad = 16u;   // debug build: a gradient index about to be written is out of range
+
+// Debug builds (-DLF_DEBUG_CHECKS), in place of a sanitizer: every index the
+// kernels are about to dereference is checked against its bound; a failure
+// sets a status bit and the access goes to index 0 instead (recorded, never a
+// trap or a fault). Release builds: the index as it is (in range by construction).
+#ifdef LF_DEBUG_CHECKS
+#define LF_DINDEX(idx, bound, status, bit) \
+    (((uint64_t)(idx) < (uint64_t)(bound)) ? (idx) : (atomicOr((status), (bit)), decltype(+(idx))(0)))
+#else
+#define LF_DINDEX(idx, bound, status, bit) (idx)
+#endif
+
 // Storage forms the kernels read (texel type x channel count).
 enum TexelKind { kF32C4 = 0, kF32C3 = 1, kF16C4 = 2, kE4M3C4 = 3 };
 

@@ -152,7 +152,7 @@ __device__ __forceinline__ bool samples_from_idx(const RenderParamsBase &p, cons
     float3 d = camera_dir(v, px, py);
     float3 ho, hd;
     if (!intersect_sphere(p.sphere, v.eye, d, ho, hd)) {
-        atomicOr(p.status, 2u);
+        atomicOr(p.status, kStatusIdxInput);
         return false;
     }
 #pragma unroll
@@ -172,7 +172,7 @@ __device__ __forceinline__ bool samples_from_idx(const RenderParamsBase &p, cons
         for (int m = 0; m < K; ++m) {
             const bool ok = (uint32_t)ix[m] < P.n;
             if (!ok && ix[m] >= 0) {
-                atomicOr(p.status, 1u);
+                atomicOr(p.status, kStatusIndex);
                 ix[m] = -1;
             }
             d2[m] = ok ? dist2_df(P, ok ? ix[m] : 0, qh, ql) : 0.0f;
@@ -266,7 +266,8 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
                 if constexpr (K == 9) {
                     if (wd[b] == 0.0f) continue;
                 }
-                float4 t = texel<DT>(p.texels, row + (uint32_t)max(jd[b], 0));
+                float4 t = texel<DT>(p.texels, LF_DINDEX(row + (uint32_t)max(jd[b], 0), (uint64_t)p.rows_valid * p.N,
+                                                          p.status, kStatusDebugTexel));
                 float2 w2 = make_float2(wd[b], wd[b]);
                 in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
                 in_zw = ffma2(w2, make_float2(t.z, t.w), in_zw);
@@ -349,6 +350,7 @@ __device__ __forceinline__ float4 group_sum_tree(float4 val, unsigned grp, unsig
 
 __device__ __forceinline__ void add_to_grad(const RenderParamsBase &p, uint64_t key, float4 sum)
 {
+    key = LF_DINDEX(key, (uint64_t)p.rows_valid * p.N, p.status, kStatusDebugGrad);
     if (p.C == 4) {
         atomicAdd(reinterpret_cast<float4 *>(p.grad) + key, sum);
     } else {

@@ -73,9 +73,11 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if not _build.up_to_date():
-                path = _build.build()
+            path = os.environ.get("LUMIPATH_LIB")      # another build of the library (e.g. debug)
+            if not path:
+                path = _build.LIB
+                if not _build.up_to_date():
+                    path = _build.build()
             if not os.path.exists(path):
                 raise RuntimeError(f"liblumipath.so is missing at {path}")
             L = C.CDLL(path)
