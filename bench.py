@@ -83,10 +83,30 @@ def _recorded():
     return rec if rec.get("csrc_sha256") == csrc_digest() else {}
 
 
+def recorded_counter(dtype: str, name: str):
+    """A recorded per-launch counter (see _recorded), or None."""
+    v = _recorded().get(f"{dtype}_{name}")
+    return int(v) if v else None
+
+
 def recorded_traffic(dtype: str):
     """DRAM bytes (read + write) per launch, or None (see _recorded)."""
-    v = _recorded().get(f"{dtype}_dram_bytes_per_launch")
-    return int(v) if v else None
+    return recorded_counter(dtype, "dram_bytes_per_launch")
+
+
+def compulsory_bytes(idx_hit, N: int, rays: int, dtype: str) -> dict:
+    """Compulsory DRAM bytes of one frame: the image (16 B per ray) plus the
+    distinct 32-byte sectors of texels and of row scales that its 25 taps per hit
+    ray touch (idx_hit: int32 [hits, 10], 5 origin then 5 direction indices)."""
+    import torch
+    tb = TEXEL_BYTES[dtype]
+    io, jd = idx_hit[:, :5].long(), idx_hit[:, 5:].long()
+    ok = (io >= 0).unsqueeze(2) & (jd >= 0).unsqueeze(1)
+    tex = (io.unsqueeze(2) * N + jd.unsqueeze(1))[ok]
+    tex_sectors = int(torch.unique((tex * tb) // 32).numel())
+    scale_sectors = int(torch.unique((io[io >= 0] * 4) // 32).numel()) if dtype != "f32" else 0
+    return {"bytes": rays * 16 + 32 * (tex_sectors + scale_sectors), "image_bytes": rays * 16,
+            "texel_sectors": tex_sectors, "scale_sectors": scale_sectors}
 
 
 def issue_roofline(dtype: str, launch_s: float):
@@ -217,13 +237,21 @@ def run_ours(args, rank: int, world: int):
     for t in tables.values():
         t.set_launch(**launch)
 
-    # hits per frame (untimed): from the index output
+    # hits per frame (untimed): from the index output; and, for the first timed
+    # frame, the compulsory DRAM bytes: the image plus every distinct 32-byte
+    # sector of texels and row scales the frame reads, each counted once
     hits = {}
+    compulsory = None
     idx_buf = torch.empty((rays, 10), dtype=torch.int32, device="cuda")
     for f, vs in frame_views.items():
         _, idx = tables["e4m3"].render(vs, with_idx=True, idx=idx_buf)
-        hits[f] = int((idx[:, 0] >= 0).sum())
-    del idx_buf
+        hit_rows = idx[:, 0] >= 0
+        hits[f] = int(hit_rows.sum())
+        if compulsory is None and f == my_frames[args.warmup]:
+            compulsory = compulsory_bytes(idx[hit_rows], N, rays, args.dtype)
+        del hit_rows
+    del idx_buf, idx
+    torch.cuda.empty_cache()
 
     outs = [torch.empty((rays, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
     stream = torch.cuda.current_stream()
@@ -387,6 +415,10 @@ def run_ours(args, rank: int, world: int):
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "kernel": f"lfk::render_kernel<{args.dtype}>", "avg_launch_ms": avg_launch_s * 1e3,
+                     "compulsory_bytes_per_launch": compulsory["bytes"] if compulsory else None,
+                     "l2_bytes_per_launch": recorded_counter(args.dtype, "l2_bytes_per_launch"),
+                     "l2_achieved_gbs": (recorded_counter(args.dtype, "l2_bytes_per_launch") or 0) / avg_launch_s / 1e9
+                     or None,
                      "issue": issue_roofline(args.dtype, avg_launch_s)},
         "clocks": clocks,
         "e2e": {"value": world * args.steps * rays / e2e_s / 1e9, "unit": UNIT,
