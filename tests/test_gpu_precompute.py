@@ -58,7 +58,7 @@ def test_small_table_matches_oracle(api):
 
 
 @pytest.mark.parametrize("case", ["rgb", "no_jitter", "empty", "sixteen_blobs", "upper_rows",
-                                  "moved_sphere", "one_step", "tiny_sets"])
+                                  "moved_sphere", "one_step", "tiny_sets", "same_sets"])
 def test_precompute_variants_match_oracle(api, case):
     M, N, C, rows = 256, 96, 4, None
     kw = dict(B=6, spp=3, steps=24)
@@ -81,6 +81,8 @@ def test_precompute_variants_match_oracle(api, case):
         rows = M // 2
     if case == "tiny_sets":
         M, N = 1, 3
+    if case == "same_sets":
+        M = N = 96          # p^o_i = p^d_i: the zero-length chord takes d = -p^o_i
     got = gpu_table(api, vol, M, N, C, rows=rows)
     want = oracle.volume_table(vol, M, N, C, rows=None if rows is None else range(rows))
     assert got.shape == want.shape
