@@ -697,12 +697,21 @@ def cpu_baseline(cfg, views, gpu_images, args, k_images=None):
         for k, img in k_images.items():
             g = img.cpu().numpy().astype(np.float64)[offs]
             psnr_k[k] = oracle.psnr(cont, g, chit & hit)
-    # the small configuration's full frame (65,536 rays, 1,024 x 256 table), all cores
-    small = lf_inputs.config_small()
-    sc_small = oracle.Scene(small.M, small.N, small.C, "lobe", lobes=small.lobes())
-    t_s = time.perf_counter()
-    oracle.render_views(sc_small, small.views, threads=cores)
-    small_rate = small.rays / (time.perf_counter() - t_s)
+    # whole frames of the two single-view cases: all cores, and one thread for the small one
+    full = {}
+    for c, single_too in ((lf_inputs.config_small(), True), (lf_inputs.config_precision(), False)):
+        scf = oracle.Scene(c.M, c.N, c.C, "lobe", lobes=c.lobes())
+        oracle.sf_points(c.M)
+        oracle.sf_points(c.N)
+        t_f = time.perf_counter()
+        oracle.render_views(scf, c.views, threads=cores)
+        entry = {"rays": c.rays, "table": f"{c.M:,} x {c.N:,}",
+                 "all_cores_value": c.rays / (time.perf_counter() - t_f) / 1e9}
+        if single_too:
+            t_f = time.perf_counter()
+            oracle.render_views(scf, c.views, threads=1)
+            entry["single_thread_value"] = c.rays / (time.perf_counter() - t_f) / 1e9
+        full[c.name] = entry
     # one host thread on a smaller sample (single-thread rate of the same oracle)
     pix1 = lf_inputs.sample_pixels(views, max(500, int(rate / cores * 2.0)), seed=13)
     t1 = time.perf_counter()
@@ -710,11 +719,11 @@ def cpu_baseline(cfg, views, gpu_images, args, k_images=None):
     single = len(pix1) / (time.perf_counter() - t1)
     base = {"value": n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "single_thread_value": single / 1e9,
-            "small_full_frame_value": small_rate / 1e9,
+            "full_frames": full,
             "sample": f"{n:,} random pixels of orbit frame 0 ({hits:,} hits), brute-force FP64 K-NN "
                       f"over all {cfg.M:,}+{cfg.N:,} SF points, texels from the FP64 lobe field; "
-                      f"{dt:.1f} s on {cores} threads; small_full_frame_value: the whole "
-                      f"{small.rays:,}-ray frame of the {small.M:,}+{small.N:,}-point case"}
+                      f"{dt:.1f} s on {cores} threads; full_frames: every pixel of the small "
+                      f"and precision cases' single views"}
     return base, psnr, psnr_k
 
 
