@@ -1,0 +1,257 @@
+"""Adversarial hit points for the index step: rays whose front and back hits are
+aimed at places where the ranking of SF points is hardest (Section 2, the 5
+(or 1, or 9) nearest points of each hit).
+
+Targets on the unit sphere, per point set:
+  * rank ties: unit vectors equidistant from the r-th and (r+1)-th nearest
+    points of a random query (the bisector of the two), r = 1 .. K;
+  * Voronoi vertices: the circumcentre direction of the 3 nearest points of a
+    random query (equidistant from all three);
+  * the poles and the rim of the pole scan (continuous index 16 from a pole);
+  * the azimuth seam (y = 0, on both sides of x);
+  * zone boundaries of the inverse mapping, where the zone number k changes.
+Each ray is the single pixel of a 1x1 view: its centre ray is the view's
+forward axis, aimed from outside S through the origin-set target T_o at the
+direction-set target T_d, so its front hit is T_o and its back hit T_d up to
+FP32 rounding. That rounding (a few 1e-7) breaks the constructed ties by a
+margin far below the tier-1 error bound of the kernel, so these rays take the
+double-float and FP64 ranking steps that random rays rarely reach. The
+expected indices are the oracle's brute force on the oracle's own FP32 ray and
+FP64 unit hits; the bar is bit-exact, order included.
+
+The construction uses scipy's k-d tree only to find neighbours; nothing of
+the method's arithmetic is involved in choosing the targets.
+"""
+import numpy as np
+import pytest
+
+import lf_inputs
+import oracle
+
+torch = pytest.importorskip("torch")
+cKDTree = pytest.importorskip("scipy.spatial").cKDTree
+
+PHI = (1.0 + 5.0 ** 0.5) / 2.0
+
+
+def _unit(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def tie_targets(P, tree, rng, count, K):
+    """Unit vectors on the bisector of the r-th and (r+1)-th nearest points of
+    a random query (r uniform in 1..K), and the rank r of each."""
+    K = min(K, len(P) - 1)
+    q = _unit(rng.standard_normal((count, 3)))
+    r = rng.integers(1, K + 1, count)
+    _, nn = tree.query(q, k=K + 1)
+    nn = nn.reshape(count, K + 1)
+    a = P[nn[np.arange(count), r - 1]]
+    b = P[nn[np.arange(count), r]]
+    u = b - a
+    q2 = q - (np.sum(q * u, 1) / np.sum(u * u, 1))[:, None] * u
+    return _unit(q2), r
+
+
+def vertex_targets(P, tree, rng, count, generators=False):
+    """Circumcentre directions of the 3 nearest points of random queries (and,
+    on request, the indices of those three). Nearly collinear triples, whose
+    circumcentre lies far from all three, are dropped."""
+    q = _unit(rng.standard_normal((3 * count, 3)))
+    _, nn = tree.query(q, k=3)
+    a, b, c = P[nn[:, 0]], P[nn[:, 1]], P[nn[:, 2]]
+    nrm = _unit(np.cross(b - a, c - a))
+    nrm = nrm * np.sign(np.sum(nrm * a, 1))[:, None]
+    keep = np.linalg.norm(nrm - a, axis=1) < 1.5 * np.sqrt(4.0 * np.pi / len(P))
+    nrm, nn = nrm[keep][:count], nn[keep][:count]
+    return (nrm, nn) if generators else nrm
+
+
+def _with_z(z, rng):
+    phi = rng.uniform(0, 2 * np.pi, len(z))
+    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([s * np.cos(phi), s * np.sin(phi), z], 1)
+
+
+def special_targets(n, rng, count):
+    """Poles, the rim of the pole scan, the azimuth seam and zone boundaries."""
+    out = []
+    sgn = lambda m: rng.choice([-1.0, 1.0], m)
+    m = count // 4
+    # at and next to the poles
+    d = 10.0 ** rng.uniform(-7, -1.5, m)
+    out.append(_with_z(sgn(m) * (1.0 - d), rng))
+    out.append(np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0], [1e-7, 0.0, 1.0], [0.0, -1e-7, -1.0]]))
+    # rim of the pole scan: continuous index (n(1 - |z|) - 1)/2 = 16
+    if n > 128:
+        z = 1.0 - 33.0 / n + rng.uniform(-1e-6, 1e-6, m)
+        out.append(_with_z(sgn(m) * z, rng))
+    # azimuth seam: y ~ 0 with x of either sign
+    z = rng.uniform(-0.99, 0.99, m)
+    y = rng.uniform(-1e-7, 1e-7, m)
+    x = sgn(m) * np.sqrt(1.0 - z * z - y * y)
+    out.append(np.stack([x, y, z], 1))
+    # zone boundaries: sqrt5 pi n (1 - z^2) = Phi^(2k)
+    ks = np.arange(2, 40)
+    w = PHI ** (2.0 * ks) / (np.sqrt(5.0) * np.pi * n)
+    w = w[w < 1.0]
+    if len(w):
+        pick = rng.choice(w, m)
+        z = np.sqrt(1.0 - pick) * (1.0 + rng.uniform(-1e-7, 1e-7, m))
+        out.append(_with_z(sgn(m) * np.minimum(z, 1.0), rng))
+    return _unit(np.concatenate(out))
+
+
+def set_targets(n, K, rng, count):
+    P = oracle.sf_points(n)
+    tree = cKDTree(P)
+    ties, _ = tie_targets(P, tree, rng, count // 2, K)
+    parts = [ties, special_targets(n, rng, count // 4)]
+    if n >= 3:
+        parts.append(vertex_targets(P, tree, rng, count // 4))
+    t = np.concatenate(parts)
+    return t[rng.permutation(len(t))]
+
+
+def chord_views(To, Td, rng):
+    """1x1 views whose pixel ray enters S at To and leaves it at Td."""
+    views = []
+    for a, b in zip(To, Td):
+        if a @ b > 0.98:                      # too short a chord: aim at the far side instead
+            b = -b
+        d = _unit(a - b)
+        eye = a + rng.uniform(0.2, 2.5) * d
+        views.append(lf_inputs.look_at(eye, b, 1, 1))
+    return lf_inputs.pack_offsets(views)
+
+
+def expected_indices(views, M, N, K):
+    """The oracle's indices of every 1x1 view: [views][2K], -1 for a miss."""
+    Po, Pd = oracle.sf_points(M), oracle.sf_points(N)
+    out = np.full((len(views), 2 * K), -1, np.int32)
+    for v, view in enumerate(views):
+        hit, _, _, _, qo, qd = oracle.trace_pixel(1.0, (0.0, 0.0, 0.0), view, 0, 0)
+        if not hit:
+            continue
+        io, _ = oracle.knn(Po, qo, K)
+        jd, _ = oracle.knn(Pd, qd, K)
+        out[v, :len(io)] = io
+        out[v, K:K + len(jd)] = jd
+    return out
+
+
+def case_views(M, N, K, count, seed):
+    rng = np.random.default_rng(seed)
+    To = set_targets(M, K, rng, count)
+    Td = set_targets(N, K, rng, count)
+    m = min(len(To), len(Td))
+    return chord_views(To[:m], Td[:m], rng)
+
+
+# --------------------------------------------------------------------------
+# The construction itself (CPU): the targets are the near-ties they claim.
+# --------------------------------------------------------------------------
+def test_tie_targets_are_equidistant_from_the_pair():
+    rng = np.random.default_rng(5)
+    for n in (300, 65536):
+        P = oracle.sf_points(n)
+        tree = cKDTree(P)
+        q, r = tie_targets(P, tree, rng, 400, 5)
+        d, nn = tree.query(q, k=7)
+        # the bisector of the r-th and (r+1)-th: some consecutive pair of the
+        # nearest points is tied to rounding (the projection may reorder ranks)
+        gaps = np.diff(d ** 2, axis=1)
+        tied = (gaps.min(axis=1) < 1e-12).mean()
+        assert tied > 0.95, f"only {tied:.1%} of the tie targets keep a tie among their 7 nearest"
+
+
+def test_vertex_targets_are_equidistant_from_three_points():
+    rng = np.random.default_rng(6)
+    P = oracle.sf_points(4096)
+    q, nn = vertex_targets(P, cKDTree(P), rng, 300, generators=True)
+    assert np.allclose(np.linalg.norm(q, axis=1), 1.0)
+    d = np.linalg.norm(q[:, None, :] - P[nn], axis=2)
+    assert np.abs(d - d[:, :1]).max() < 1e-12
+    # a local vertex: on the side of the three points, within 1.5 sigma of them
+    assert len(q) == 300 and np.all(d < 1.5 * np.sqrt(4.0 * np.pi / 4096))
+
+
+def test_special_targets_sit_where_they_claim():
+    rng = np.random.default_rng(7)
+    n = 65536
+    t = special_targets(n, rng, 4000)
+    assert np.allclose(np.linalg.norm(t, axis=1), 1.0)
+    z = t[:, 2]
+    ic = (n * (1.0 - np.abs(z)) - 1.0) / 2.0
+    assert np.any(np.abs(ic - 16.0) < 1e-3), "no target on the rim of the pole scan"
+    assert np.any(np.abs(t[:, 1]) < 2e-7), "no target on the azimuth seam"
+    zone = np.log(np.sqrt(5.0) * np.pi * n * np.maximum(1.0 - z * z, 1e-300)) / np.log(PHI ** 2)
+    assert np.any(np.abs(zone - np.round(zone)) < 1e-5), "no target on a zone boundary"
+
+
+def test_chord_views_hit_their_targets():
+    """The oracle's FP32 ray of each 1x1 view enters S at T_o and leaves at T_d."""
+    rng = np.random.default_rng(8)
+    To = _unit(rng.standard_normal((200, 3)))
+    Td = _unit(rng.standard_normal((200, 3)))
+    views = chord_views(To, Td, np.random.default_rng(9))
+    for v, a, b in zip(views, To, Td):
+        if a @ b > 0.98:
+            b = -b
+        hit, _, _, _, qo, qd = oracle.trace_pixel(1.0, (0.0, 0.0, 0.0), v, 0, 0)
+        assert hit
+        assert np.linalg.norm(qo - a) < 2e-6 and np.linalg.norm(qd - b) < 2e-6
+
+
+def test_ties_survive_the_fp32_ray():
+    """After the FP32 ray step most targets keep a rank gap below the FP32 error
+    of a squared distance (about 2^-20 d), which the kernel cannot order at its
+    first tier, and many a gap below the double-float error (about 2^-18 d^2),
+    which leaves the order to its FP64 step."""
+    M, N, K = 65536, 4096, 5
+    views = case_views(M, N, K, 600, seed=10)
+    Po, Pd = oracle.sf_points(M), oracle.sf_points(N)
+    tier1 = tier2 = total = 0
+    for view in views:
+        hit, _, _, _, qo, qd = oracle.trace_pixel(1.0, (0.0, 0.0, 0.0), view, 0, 0)
+        assert hit
+        for P, q in ((Po, qo), (Pd, qd)):
+            d2 = np.sort(np.sum((P - q) ** 2, axis=1))[:K + 2]
+            gap, d2n = np.diff(d2)[:K], d2[1:K + 1]
+            tier1 += np.any(gap < 2.0 ** -20 * np.sqrt(d2n))
+            tier2 += np.any(gap < 2.0 ** -18 * d2n)
+            total += 1
+    assert tier1 >= 0.4 * total, f"{tier1} of {total} searches near-tied at the FP32 error"
+    assert tier2 >= 0.1 * total, f"{tier2} of {total} searches near-tied at the double-float error"
+
+
+# --------------------------------------------------------------------------
+# GPU against the oracle
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_03837_gb300 import torch_api
+    return torch_api
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("M,N,K", [(262144, 256, 5), (65536, 4096, 5), (1024, 131072, 5), (300, 1000, 5),
+                                   (100, 60, 5), (16384, 4096, 9), (300, 200, 9), (65536, 4096, 1),
+                                   (1000, 300, 1)])
+def test_adversarial_hits_bit_exact(api, M, N, K):
+    views = case_views(M, N, K, 12000, seed=M * 31 + N * 7 + K)
+    want = expected_indices(views, M, N, K)
+    codes = torch.zeros((M, N, 4), dtype=torch.uint8, device="cuda")
+    lf = api.LightField(codes, "e4m3", torch.ones((M,), device="cuda"), borrow=True, k_nearest=K)
+    _, idx = lf.render(views, with_idx=True)
+    lf.sync_status()
+    got = idx.cpu().numpy()
+    lf.close()
+    del codes
+    assert got.shape == want.shape
+    assert (want[:, 0] >= 0).mean() > 0.99
+    bad = np.nonzero(np.any(got != want, axis=1))[0]
+    assert len(bad) == 0, (f"{len(bad)} of {len(views)} adversarial rays differ; first "
+                           f"{[(int(b), got[b].tolist(), want[b].tolist()) for b in bad[:3]]}")
