@@ -471,7 +471,7 @@ def sm_max_mhz() -> float:
 
 
 def run_precompute(args):
-    """Light-field precompute (Section 3) of the analytic volume scene into a
+    """Light-field precompute (Section 2) of the analytic volume scene into a
     16,384 x 512 RGBA FP32 table: 8 blobs, 4 jittered samples per texel, 64
     midpoint steps. ALU-bound: the roofline counts the algorithm's FP32 lane
     operations per midpoint step -- per blob, 2 for the blob's exponent (a
@@ -508,6 +508,7 @@ def run_precompute(args):
     fp32_peak = sms * 128 * mhz * 1e6 / 1e12
     xu_peak = sms * 32 * mhz * 1e6 / 1e12
     achieved = fp32_ops / (ms * 1e-3) / 1e12
+    versus = light_field_vs_direct(args, vol, cfg.views, out)
     del out
     return {"workload": f"precompute: {M:,} x {N:,} RGBA FP32 table of a {vol.B}-blob emission-absorption "
                         f"volume, {vol.spp} jittered samples per texel, {vol.steps} midpoint steps",
@@ -518,7 +519,63 @@ def run_precompute(args):
                          "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz",
                          "exp2_per_s_T": exp2s / (ms * 1e-3) / 1e12,
                          "exp2_frac_of_32_per_sm_clk": exp2s / (ms * 1e-3) / 1e12 / xu_peak,
-                         "kernel": "lfk::precompute_kernel<8>"}}
+                         "kernel": "lfk::precompute_kernel<8>"},
+            "light_field_vs_direct": versus}
+
+
+def light_field_vs_direct(args, vol, views, table):
+    """The light field against the scene itself: the direct render of the
+    volume along every pixel's ray (lf_render_volume, the ground truth) and the
+    light-field render of the precomputed table for the same views, both timed
+    with CUDA events, and the PSNR of the light-field image against the direct
+    one over the hit pixels -- for the given table and for a larger one."""
+    import torch
+    from paper_1903_03837_gb300 import torch_api as api
+    st = torch.cuda.current_stream()
+    rays = lf_inputs.total_pixels(views)
+    reps = max(3, min(args.steps, 10))
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    gt = torch.empty((rays, 4), device="cuda")
+    direct_ms = timed(lambda: api.render_volume(vol, views, 4, out=gt))
+    gt_np = gt.cpu().numpy()
+    img = torch.empty((rays, 4), device="cuda")
+    res = {"views": f"{len(views)} views, {rays:,} rays", "steps": vol.steps,
+           "direct_ms": direct_ms, "direct_grays_s": rays / (direct_ms * 1e-3) / 1e9, "tables": {}}
+    M0, N0 = int(table.shape[0]), int(table.shape[1])
+    for M, N in ((M0, N0), (4 * M0, 4 * N0)):
+        T = table if (M, N) == (M0, N0) else api.precompute_table(vol, M, N, 4)
+        lf = api.LightField(T, "f32", borrow=True)
+        lf.set_launch(tile_w=16, tile_h=8, warp_w=8)
+        _, idx = lf.render(views, out=img, with_idx=True)
+        hit = idx[:, 0].cpu().numpy() >= 0
+        ms = timed(lambda: lf.render(views, out=img))
+        res["tables"][f"{M:,} x {N:,}"] = {
+            "light_field_ms": ms, "light_field_grays_s": rays / (ms * 1e-3) / 1e9,
+            "psnr_vs_direct_db": psnr_db(gt_np[:, :3], img.cpu().numpy()[:, :3], hit),
+            "hit_fraction": float(hit.mean())}
+        lf.close()
+        del T
+    return res
+
+
+def psnr_db(ref, test, hit):
+    """10 log10(peak^2 / MSE) over the hit pixels' channels, peak = max of ref there."""
+    r = np.asarray(ref, np.float64)[hit]
+    t = np.asarray(test, np.float64)[hit]
+    mse = float(np.mean((r - t) ** 2))
+    return float("inf") if mse == 0.0 else 10.0 * math.log10(float(r.max()) ** 2 / mse)
 
 
 def run_fit_steps(args):

@@ -209,7 +209,7 @@ lf_status lf_fill_lobe_table(uint32_t M, uint32_t N, uint32_t C, uint32_t L,
                              float *out_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Light-field precompute (Section 3): fill L^(i,j) by tracing every ray
+ * Light-field precompute (Section 2): fill L^(i,j) by tracing every ray
  *   r_k = (O + R p^o_i) + t d_ij,  d_ij = (p^d_j - p^o_i) / |p^d_j - p^o_i|
  * (-p^o_i if the two points coincide) through an analytic scene inside S, with
  * the origin of each of `spp` samples jittered uniformly on the disk of area
@@ -263,6 +263,23 @@ typedef struct {
  * LF_ERR_OUT_OF_MEMORY, LF_ERR_CUDA. Asynchronous on `stream`. */
 lf_status lf_precompute_table(const lf_precompute_desc *desc, const lf_blob *blobs_host,
                               float *out_dev, void *stream);
+
+/* Direct render of the same volume: the ground truth that a light-field render
+ * of the precomputed table approximates (the paper compares its renders with
+ * path-traced images of the scene, Section 3). For every pixel of the views the
+ * camera ray and its front hit h_o on S are the FP32 steps of lf_render; the
+ * ray is then integrated as above from h_o along its direction to the far
+ * intersection with S (that length computed in FP64), one sample, no jitter.
+ * out_dev [pixels][channels] FP32 (device, caller-owned; RGB, plus opacity
+ * 1 - T for channels = 4), written at each view's out_offset; misses store 0.
+ * Reads radius, center, channels, steps, n_blobs and the background of
+ * `desc`; n_origins, n_directions, rows, spp, jitter and seed are ignored.
+ * out_dev must be 16-byte aligned for 4 channels, 4-byte for 3. One kernel
+ * launch per view; allocates nothing. Errors: LF_ERR_INVALID_ARG (NULL,
+ * ranges, non-finite values, views as for lf_render), LF_ERR_CUDA.
+ * Asynchronous on `stream`. */
+lf_status lf_render_volume(const lf_precompute_desc *desc, const lf_blob *blobs_host,
+                           const lf_view *views_host, uint32_t n_views, float *out_dev, void *stream);
 
 /* Largest M + N that lf_render_noalloc accepts. */
 #define LF_NOALLOC_MAX_POINTS 278528u

@@ -18,9 +18,11 @@ marshals numpy arrays through ctypes. Functions:
 * ``render_backward``                        -- adjoint of the blend w.r.t. the table
 * ``f16_*``, ``e4m3_*``, ``quantize_rows``   -- per-row FP16 / E4M3 table storage
 * ``lobe_table``                             -- the synthetic lobe radiance field
-* ``volume_table``, ``volume_ray``, ``volume_origin`` -- light-field precompute (Section 3):
+* ``volume_table``, ``volume_ray``, ``volume_origin`` -- light-field precompute (Section 2):
   every ray r_k through an emission-absorption volume of Gaussian blobs, origins
   jittered on the disk of area A_S/M
+* ``volume_pixels``                          -- direct render of that volume along each
+  pixel's ray (the ground truth of a light-field render of the precomputed table)
 * ``psnr``                                   -- image error against an FP64 render
 
 Parity unpinned: none. Each function is pinned in ``tests/test_oracle_pins.py``.
@@ -106,6 +108,7 @@ def lib():
                 "lfo_volume_ray": (None, [vp, vp, vp, vp, vp]),
                 "lfo_volume_texel": (None, [vp, vp, vp, u32, u32, u32, u32, vp]),
                 "lfo_volume_table_rows": (None, [vp, vp, vp, u32, u32, u32, u32, vp]),
+                "lfo_volume_pixels": (i64, [vp, vp, vp, vp, i64, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -335,7 +338,7 @@ def lobe_table(lobes, M: int, N: int, rows: Optional[Sequence[int]] = None,
 
 
 # --------------------------------------------------------------------------
-# Light-field precompute (Section 3): volume scene
+# Light-field precompute (Section 2): volume scene
 # --------------------------------------------------------------------------
 class _Volume(C.Structure):
     _fields_ = [("B", C.c_uint32), ("C", C.c_uint32), ("spp", C.c_uint32), ("steps", C.c_uint32),
@@ -405,6 +408,30 @@ def volume_table(vol, M: int, N: int, C_: int = 4, rows: Optional[Sequence[int]]
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(one, range(len(rows))))
     return out
+
+
+def volume_pixels(vol, views, pix: np.ndarray, C_: int = 4, threads: Optional[int] = None):
+    """Direct render of the volume at pixels pix [n,3] = (view, x, y): each
+    pixel's ray from its front hit on S to the far intersection, one sample,
+    no jitter. (out [n,C] FP64 -- RGB, plus opacity 1 - T for C = 4 --, hits);
+    misses are 0."""
+    h = _VolumeHold(vol, C_)
+    pix = np.ascontiguousarray(pix, np.uint32)
+    n = pix.shape[0]
+    vf, wh = _views_arrays(views)
+    out = np.zeros((n, C_))
+    L = lib()
+    nt = min(_threads(threads), max(1, n // 64))
+    bounds = np.linspace(0, n, nt * 4 + 1).astype(np.int64)
+
+    def work(k):
+        a, b = int(bounds[k]), int(bounds[k + 1])
+        if b <= a:
+            return 0
+        return L.lfo_volume_pixels(C.byref(h.s), _p(vf), _p(wh), _p(pix[a:]), b - a, _p(out[a:]))
+    with ThreadPoolExecutor(nt) as ex:
+        hits = sum(ex.map(work, range(len(bounds) - 1)))
+    return out, int(hits)
 
 
 # --------------------------------------------------------------------------

@@ -22,7 +22,7 @@
  *   - the adjoint of that blend with respect to the table (gradient of a linear map).
  *   - the synthetic lobe radiance field used as input, and the FP16 / FP8-E4M3
  *     per-row quantisers written from the IEEE 754 binary16 and OCP E4M3FN definitions.
- *   - the light-field precompute (Section 3, equation of r_k; origins jittered on a
+ *   - the light-field precompute (Section 2, equation of r_k; origins jittered on a
  *     disk of area A_S/M): every ray r_k traced through an analytic emission-absorption
  *     volume (Gaussian blobs), midpoint rule, mean over jittered samples.
  *
@@ -522,7 +522,7 @@ int lfo_trace_pixel(double R, const double O[3], const float *vw, uint32_t W, ui
 }
 
 /* ------------------------------------------------------------------------- */
-/* Light-field precompute (Section 3): L^(i,j) is the radiance a camera ray   */
+/* Light-field precompute (Section 2): L^(i,j) is the radiance a camera ray   */
 /* r_k = (O + R p^o_i) + t d_ij, d_ij = (p^d_j - p^o_i)/|p^d_j - p^o_i|,       */
 /* collects inside S; each of `spp` samples moves the origin uniformly on a   */
 /* disk of area A_S / M = 4 pi R^2 / M tangent to S at O + R p^o_i, and the   */
@@ -655,4 +655,31 @@ void lfo_volume_table_rows(const lfo_volume *V, const double *Po, const double *
             for (uint32_t c = 0; c < V->C; ++c)
                 out[(((size_t)(i - i0)) * N + j) * V->C + c] = (float)v[c];
         }
+}
+
+/* Direct render of the volume (the ground truth a light-field render of the  */
+/* precomputed table approximates): each pixel's camera ray and front hit     */
+/* h_o on S as above (FP32), then the same emission-absorption integral from   */
+/* h_o along the ray's direction to the far intersection with S (one sample,   */
+/* no jitter). out: [np][C] FP64, RGB (+ opacity 1 - T); misses store 0.       */
+/* Returns the number of hits.                                                 */
+int64_t lfo_volume_pixels(const lfo_volume *V, const float *views, const uint32_t *wh,
+                          const uint32_t *pix, int64_t np, double *out)
+{
+    int64_t hits = 0;
+    float O32[3] = {(float)V->O[0], (float)V->O[1], (float)V->O[2]};
+    for (int64_t p = 0; p < np; ++p) {
+        uint32_t v = pix[3 * p], x = pix[3 * p + 1], y = pix[3 * p + 2];
+        const float *vw = views + 14 * v;
+        float dir[3], ho[3], hd[3];
+        for (uint32_t c = 0; c < V->C; ++c) out[p * V->C + c] = 0.0;
+        lfo_camera_ray(vw, wh[2 * v], wh[2 * v + 1], x, y, dir);
+        if (!lfo_intersect((float)V->R, O32, vw, dir, ho, hd)) continue;
+        ++hits;
+        double o[3] = {ho[0], ho[1], ho[2]}, d[3] = {dir[0], dir[1], dir[2]}, rgb[3], T;
+        lfo_volume_ray(V, o, d, rgb, &T);
+        for (int c = 0; c < 3; ++c) out[p * V->C + c] = rgb[c];
+        if (V->C == 4) out[p * V->C + 3] = 1.0 - T;
+    }
+    return hits;
 }

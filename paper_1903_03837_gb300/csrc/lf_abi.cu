@@ -66,6 +66,53 @@ lf_launch default_launch()
     return l;
 }
 
+// Volume fields of a precompute description (radius, centre, channels,
+// steps, blobs, background) checked and turned into kernel parameters; the
+// SF-set fields are left to the caller.
+lf_status volume_params(const lf_precompute_desc *d, const lf_blob *blobs, float *out_dev,
+                        lfk::PrecomputeParams &P)
+{
+    if (!(d->radius > 0.0) || !std::isfinite(d->radius) || !std::isfinite(d->center[0]) ||
+        !std::isfinite(d->center[1]) || !std::isfinite(d->center[2]))
+        return fail(LF_ERR_INVALID_ARG, "R must be positive and finite, O finite");
+    if (d->channels != 3 && d->channels != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4");
+    if (d->steps == 0 || d->steps > 4096) return fail(LF_ERR_INVALID_ARG, "steps must be in [1, 4096]");
+    if (d->n_blobs > LF_PRECOMPUTE_MAX_BLOBS)
+        return fail(LF_ERR_INVALID_ARG, "at most %u blobs", LF_PRECOMPUTE_MAX_BLOBS);
+    if (d->n_blobs && !blobs) return fail(LF_ERR_INVALID_ARG, "blobs is NULL");
+    if (misaligned(out_dev, d->channels == 4 ? 16 : 4))
+        return fail(LF_ERR_INVALID_ARG, "out must be %u-byte aligned for %u channels",
+                    d->channels == 4 ? 16u : 4u, d->channels);
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(d->bg0[k]) || !std::isfinite(d->bg1[k]))
+            return fail(LF_ERR_INVALID_ARG, "non-finite background");
+    memset(&P, 0, sizeof P);
+    for (uint32_t b = 0; b < d->n_blobs; ++b) {
+        const lf_blob &B = blobs[b];
+        bool ok = B.width > 0.0f && std::isfinite(B.width) && B.density >= 0.0f && std::isfinite(B.density);
+        for (int k = 0; k < 3; ++k) ok = ok && std::isfinite(B.center[k]) && std::isfinite(B.emit[k]);
+        if (!ok) return fail(LF_ERR_INVALID_ARG, "blob %u: non-finite value, width <= 0 or density < 0", b);
+        // density kappa exp(-r^2 / (2 s^2)) = exp2(log2(kappa) - (a r)^2), a^2 = log2(e) / (2 s^2)
+        const double a = std::sqrt(1.4426950408889634 / 2.0) / (double)B.width;
+        P.blob_pos[b] = make_float4(B.center[0], B.center[1], B.center[2],
+                                    B.density > 0.0f ? (float)std::log2((double)B.density) : -INFINITY);
+        P.blob_col[b] = make_float4(B.emit[0], B.emit[1], B.emit[2], (float)a);
+    }
+    P.out = out_dev;
+    P.Ox = (float)d->center[0];
+    P.Oy = (float)d->center[1];
+    P.Oz = (float)d->center[2];
+    P.R = (float)d->radius;
+    P.C = d->channels;
+    P.steps = d->steps;
+    P.nb = d->n_blobs;
+    for (int k = 0; k < 3; ++k) {
+        P.bg0[k] = d->bg0[k];
+        P.bg1[k] = d->bg1[k];
+    }
+    return LF_OK;
+}
+
 lf_status check_launch(const lf_launch *c)
 {
     if (!c) return fail(LF_ERR_INVALID_ARG, "launch config is NULL");
@@ -104,9 +151,11 @@ lf_status check_views(const lf_view *views, uint32_t n)
     return LF_OK;
 }
 
-lfk::ViewK to_viewk(const lf_view &w, const lf_launch &L, const lf_table *t)
+// The camera of a view (no tiling, no miss constants).
+lfk::ViewK camera_of(const lf_view &w)
 {
     lfk::ViewK k;
+    memset(&k, 0, sizeof k);
     for (int i = 0; i < 3; ++i) {
         k.eye[i] = w.eye[i];
         k.right[i] = w.right[i];
@@ -118,6 +167,12 @@ lfk::ViewK to_viewk(const lf_view &w, const lf_launch &L, const lf_table *t)
     k.width = w.width;
     k.height = w.height;
     k.out_offset = w.out_offset;
+    return k;
+}
+
+lfk::ViewK to_viewk(const lf_view &w, const lf_launch &L, const lf_table *t)
+{
+    lfk::ViewK k = camera_of(w);
     k.tiles_x = (w.width + L.tile_w - 1) / L.tile_w;
     k.tiles_y = (w.height + L.tile_h - 1) / L.tile_h;
     lfk::fill_view_miss_consts(k, t->desc.radius, t->desc.center);
@@ -531,53 +586,18 @@ lf_status lf_precompute_table(const lf_precompute_desc *d, const lf_blob *blobs,
     if (!out_dev) return fail(LF_ERR_INVALID_ARG, "out is NULL");
     const uint32_t M = d->n_origins, N = d->n_directions;
     if (M == 0 || N == 0 || M > (1u << 24) || N > (1u << 24)) return fail(LF_ERR_INVALID_ARG, "bad M/N");
-    if (!(d->radius > 0.0) || !std::isfinite(d->radius) || !std::isfinite(d->center[0]) ||
-        !std::isfinite(d->center[1]) || !std::isfinite(d->center[2]))
-        return fail(LF_ERR_INVALID_ARG, "R must be positive and finite, O finite");
-    if (d->channels != 3 && d->channels != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4");
     if (d->rows == 0 || d->rows > M) return fail(LF_ERR_INVALID_ARG, "rows must be in [1, M] (got %u)", d->rows);
     if (d->spp == 0 || d->spp > 1024) return fail(LF_ERR_INVALID_ARG, "spp must be in [1, 1024]");
-    if (d->steps == 0 || d->steps > 4096) return fail(LF_ERR_INVALID_ARG, "steps must be in [1, 4096]");
     if (d->jitter > 1) return fail(LF_ERR_INVALID_ARG, "jitter must be 0 or 1");
-    if (d->n_blobs > LF_PRECOMPUTE_MAX_BLOBS)
-        return fail(LF_ERR_INVALID_ARG, "at most %u blobs", LF_PRECOMPUTE_MAX_BLOBS);
-    if (d->n_blobs && !blobs) return fail(LF_ERR_INVALID_ARG, "blobs is NULL");
-    if (d->channels == 4 && ((uintptr_t)out_dev & 15u))
-        return fail(LF_ERR_INVALID_ARG, "out must be 16-byte aligned for 4 channels");
-    for (int k = 0; k < 3; ++k)
-        if (!std::isfinite(d->bg0[k]) || !std::isfinite(d->bg1[k]))
-            return fail(LF_ERR_INVALID_ARG, "non-finite background");
     static thread_local lfk::PrecomputeParams P;
-    memset(&P, 0, sizeof P);
-    for (uint32_t b = 0; b < d->n_blobs; ++b) {
-        const lf_blob &B = blobs[b];
-        bool ok = B.width > 0.0f && std::isfinite(B.width) && B.density >= 0.0f && std::isfinite(B.density);
-        for (int k = 0; k < 3; ++k) ok = ok && std::isfinite(B.center[k]) && std::isfinite(B.emit[k]);
-        if (!ok) return fail(LF_ERR_INVALID_ARG, "blob %u: non-finite value, width <= 0 or density < 0", b);
-        // density kappa exp(-r^2 / (2 s^2)) = exp2(log2(kappa) - (a r)^2), a^2 = log2(e) / (2 s^2)
-        const double a = std::sqrt(1.4426950408889634 / 2.0) / (double)B.width;
-        P.blob_pos[b] = make_float4(B.center[0], B.center[1], B.center[2],
-                                    B.density > 0.0f ? (float)std::log2((double)B.density) : -INFINITY);
-        P.blob_col[b] = make_float4(B.emit[0], B.emit[1], B.emit[2], (float)a);
-    }
-    P.out = out_dev;
-    P.Ox = (float)d->center[0];
-    P.Oy = (float)d->center[1];
-    P.Oz = (float)d->center[2];
-    P.R = (float)d->radius;
+    lf_status s = volume_params(d, blobs, out_dev, P);
+    if (s != LF_OK) return s;
     P.disk_r = (float)(2.0 * d->radius / std::sqrt((double)M));
     P.N = N;
-    P.C = d->channels;
     P.rows = d->rows;
     P.spp = d->spp;
-    P.steps = d->steps;
     P.jitter = d->jitter;
-    P.nb = d->n_blobs;
     P.seed = d->seed;
-    for (int k = 0; k < 3; ++k) {
-        P.bg0[k] = d->bg0[k];
-        P.bg1[k] = d->bg1[k];
-    }
     cudaStream_t st = (cudaStream_t)stream;
     float4 *pts = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&pts, sizeof(float4) * 2ull * ((uint64_t)M + N), st);
@@ -592,6 +612,28 @@ lf_status lf_precompute_table(const lf_precompute_desc *d, const lf_blob *blobs,
     cudaError_t e2 = cudaFreeAsync(pts, st);
     if (e != cudaSuccess) return cuda_fail(e, "precompute");
     if (e2 != cudaSuccess) return cuda_fail(e2, "point free");
+    return LF_OK;
+}
+
+lf_status lf_render_volume(const lf_precompute_desc *d, const lf_blob *blobs, const lf_view *views,
+                           uint32_t n_views, float *out_dev, void *stream)
+{
+    NvtxRange nvtx_("lf_render_volume");
+    g_err.clear();
+    if (!d) return fail(LF_ERR_INVALID_ARG, "desc is NULL");
+    if (!out_dev) return fail(LF_ERR_INVALID_ARG, "out is NULL");
+    static thread_local lfk::PrecomputeParams P;
+    lf_status s = volume_params(d, blobs, out_dev, P);
+    if (s != LF_OK) return s;
+    s = check_views(views, n_views);
+    if (s != LF_OK) return s;
+    lfk::SphereK S;
+    lfk::fill_sphere_consts(S, d->radius, d->center);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (uint32_t v = 0; v < n_views; ++v) {
+        cudaError_t e = lfk::launch_volume_direct(P, camera_of(views[v]), S, d->radius, st);
+        if (e != cudaSuccess) return cuda_fail(e, "direct volume render");
+    }
     return LF_OK;
 }
 

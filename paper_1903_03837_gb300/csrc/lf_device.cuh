@@ -649,7 +649,7 @@ __device__ __forceinline__ void insert_sorted(uint32_t (&s)[N], uint32_t key)
     }
 }
 
-__device__ __noinline__ TopK<9> knn9_fp64(const PointSetK P, const SphereK S, float3 h, const Source src,
+static __device__ __noinline__ TopK<9> knn9_fp64(const PointSetK P, const SphereK S, float3 h, const Source src,
                                           float3 qh, float3 ql)
 {
     double q[3];
@@ -691,7 +691,7 @@ struct Keys10 {
     uint32_t k[10];
 };
 
-__device__ __noinline__ TopK<9> knn9_rerank(const PointSetK P, const SphereK S, float3 h, const Source src,
+static __device__ __noinline__ TopK<9> knn9_rerank(const PointSetK P, const SphereK S, float3 h, const Source src,
                                             float3 qh, float3 ql, const Keys10 s10, uint32_t mask1)
 {
     constexpr uint32_t kNone = 0xffffffffu;

@@ -74,7 +74,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t ctr)
     return z ^ (z >> 31);
 }
 
-// lf_precompute.cu: the light-field precompute of Section 3 (volume scene).
+// lf_precompute.cu: the light-field precompute of Section 2 (volume scene).
 constexpr int kMaxBlobs = 16;
 struct PrecomputeParams {
     const float4 *po_hi, *po_lo, *pd_hi, *pd_lo;   // SF points (hi + lo parts)
@@ -88,6 +88,11 @@ struct PrecomputeParams {
     float4 blob_col[kMaxBlobs];    // emit rgb, a_b = sqrt(log2(e) / 2) / s_b
 };
 cudaError_t launch_precompute(const PrecomputeParams &p, cudaStream_t st);
+// Direct render of the precompute's volume along the pixel rays of one view
+// (out at the view's out_offset; p.out, p.C and the volume fields are used;
+// R is the radius in FP64 for the far end of each ray).
+cudaError_t launch_volume_direct(const PrecomputeParams &p, const ViewK &v, const SphereK &S, double R,
+                                 cudaStream_t st);
 
 // Fills the conservative-miss constants of a view for sphere (R, O) (lf_abi.cu).
 void fill_view_miss_consts(ViewK &k, double R, const double O[3]);

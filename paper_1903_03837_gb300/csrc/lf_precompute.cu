@@ -1,4 +1,4 @@
-// lf_precompute.cu -- the light-field precompute of Section 3: every ray
+// lf_precompute.cu -- the light-field precompute of Section 2: every ray
 // r_k = (O + R p^o_i) + t d_ij of the two SF point sets, with its origin
 // jittered on the disk of area A_S / M tangent to S, traced through an
 // analytic emission-absorption volume of Gaussian blobs; L^(i,j) is the mean
@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "lf_device.cuh"
 #include "lf_kernels.h"
 
 namespace lfk {
@@ -89,6 +90,105 @@ __device__ __forceinline__ float one_minus_exp_over_x(float x, float E)
 #endif
 constexpr int kPreStepUnroll = LF_PRE_STEP_UNROLL;
 
+// Radiance collected along o + t d, t in [0, t_end], by the midpoint rule with
+// p.steps steps of constant density and emission (see the top of the file):
+// (RGB including the background seen through the final transmittance T, and
+// 1 - T).
+template <int BMAX>
+__device__ __forceinline__ float4 march(const PrecomputeParams &p, float ox, float oy, float oz, float dx,
+                                        float dy, float dz, float t_end)
+{
+    const float dt = t_end / (float)p.steps;
+    // per-blob constants of this ray
+    float y0[BMAX], dy0[BMAX], la[BMAX], G[BMAX];
+#pragma unroll
+    for (int k = 0; k < BMAX; ++k) {
+        const float4 bp = p.blob_pos[k];
+        const float a = p.blob_col[k].w;
+        const float fx = ox - bp.x, fy = oy - bp.y, fz = oz - bp.z;
+        const float along = fmaf(fx, dx, fmaf(fy, dy, fz * dz));
+        const float cx = fy * dz - fz * dy, cy = fz * dx - fx * dz, cz = fx * dy - fy * dx;
+        const float perp = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+        y0[k] = a * fmaf(0.5f, dt, along);
+        dy0[k] = a * dt;
+        la[k] = (k < (int)p.nb) ? fmaf(-a * a, perp, bp.w) : -INFINITY;
+        G[k] = 0.0f;
+    }
+
+    float T = 1.0f;
+    if (dt > 0.0f) {
+#if LF_PRE_PACKED
+        // blobs in pairs: y, y^2, the exponent, the density sum and the
+        // per-blob weights in packed FP32 pairs
+        constexpr int BP = BMAX / 2;
+        float2 Y0[BP], DY[BP], LA[BP], G2[BP];
+#pragma unroll
+        for (int q = 0; q < BP; ++q) {
+            Y0[q] = make_float2(y0[2 * q], y0[2 * q + 1]);
+            DY[q] = make_float2(dy0[2 * q], dy0[2 * q + 1]);
+            LA[q] = make_float2(la[2 * q], la[2 * q + 1]);
+            G2[q] = make_float2(0.0f, 0.0f);
+        }
+        float kf = 0.0f;
+#pragma unroll kPreStepUnroll
+        for (uint32_t st = 0; st < p.steps; ++st, kf += 1.0f) {
+            const float2 kf2 = make_float2(kf, kf);
+            float2 g2[BP], sig2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int q = 0; q < BP; ++q) {
+                const float2 y = fma2(kf2, DY[q], Y0[q]);
+                const float2 arg = sub2(LA[q], mul2(y, y));
+                g2[q] = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                sig2 = add2(sig2, g2[q]);
+            }
+            // step of constant density: weight T (1 - e^-x) / sigma = T dt (1 - e^-x) / x
+            const float xs = (sig2.x + sig2.y) * dt;
+            const float E = ex2_approx(-xs * kLog2e);
+            const float w = T * one_minus_exp_over_x(xs, E) * dt;
+            const float2 w2 = make_float2(w, w);
+#pragma unroll
+            for (int q = 0; q < BP; ++q) G2[q] = fma2(w2, g2[q], G2[q]);
+            T *= E;
+        }
+#pragma unroll
+        for (int q = 0; q < BP; ++q) {
+            G[2 * q] = G2[q].x;
+            G[2 * q + 1] = G2[q].y;
+        }
+#else
+        float kf = 0.0f;
+#pragma unroll kPreStepUnroll
+        for (uint32_t st = 0; st < p.steps; ++st, kf += 1.0f) {
+            float g[BMAX], sig = 0.0f;
+#pragma unroll
+            for (int k = 0; k < BMAX; ++k) {
+                const float y = fmaf(kf, dy0[k], y0[k]);
+                g[k] = ex2_approx(fmaf(-y, y, la[k]));
+                sig += g[k];
+            }
+            // step of constant density: weight T (1 - e^-x) / sigma = T dt (1 - e^-x) / x
+            const float xs = sig * dt;
+            const float E = ex2_approx(-xs * kLog2e);
+            const float w = T * one_minus_exp_over_x(xs, E) * dt;
+#pragma unroll
+            for (int k = 0; k < BMAX; ++k) G[k] = fmaf(w, g[k], G[k]);
+            T *= E;
+        }
+#endif
+    }
+    float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < BMAX; ++k) {
+        const float4 bc = p.blob_col[k];
+        L0 = fmaf(G[k], bc.x, L0);
+        L1 = fmaf(G[k], bc.y, L1);
+        L2 = fmaf(G[k], bc.z, L2);
+    }
+    const float bgw = 0.5f * (1.0f + dz);
+    return make_float4(fmaf(T, fmaf(p.bg1[0], bgw, p.bg0[0]), L0), fmaf(T, fmaf(p.bg1[1], bgw, p.bg0[1]), L1),
+                       fmaf(T, fmaf(p.bg1[2], bgw, p.bg0[2]), L2), 1.0f - T);
+}
+
 template <int BMAX>
 __global__ void __launch_bounds__(256, BMAX <= 8 ? LF_PRE_MIN_BLOCKS : 1)
     precompute_kernel(const __grid_constant__ PrecomputeParams p)
@@ -120,7 +220,6 @@ __global__ void __launch_bounds__(256, BMAX <= 8 ? LF_PRE_MIN_BLOCKS : 1)
         const float ephx = -py * irho, ephy = px * irho;
         const float ethx = px * pz * irho, ethy = py * pz * irho, ethz = -rho2 * irho;
         const float pd = fmaf(px, dx, fmaf(py, dy, pz * dz));    // p . d
-        const float bgw = 0.5f * (1.0f + dz);
 
         float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
         for (uint32_t s = 0; s < p.spp; ++s) {
@@ -147,97 +246,12 @@ __global__ void __launch_bounds__(256, BMAX <= 8 ? LF_PRE_MIN_BLOCKS : 1)
             const float c = fmaf(offx, offx, fmaf(offy, offy, offz * offz));
             const float disc = fmaf(b, b, -c);
             const float t_end = disc > 0.0f ? fmaxf(0.0f, sqrtf(disc) - b) : 0.0f;
-            const float dt = t_end / (float)p.steps;
 
-            // per-blob constants of this ray
-            float y0[BMAX], dy0[BMAX], la[BMAX], G[BMAX];
-#pragma unroll
-            for (int k = 0; k < BMAX; ++k) {
-                const float4 bp = p.blob_pos[k];
-                const float a = p.blob_col[k].w;
-                const float fx = ox - bp.x, fy = oy - bp.y, fz = oz - bp.z;
-                const float along = fmaf(fx, dx, fmaf(fy, dy, fz * dz));
-                const float cx = fy * dz - fz * dy, cy = fz * dx - fx * dz, cz = fx * dy - fy * dx;
-                const float perp = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-                y0[k] = a * fmaf(0.5f, dt, along);
-                dy0[k] = a * dt;
-                la[k] = (k < (int)p.nb) ? fmaf(-a * a, perp, bp.w) : -INFINITY;
-                G[k] = 0.0f;
-            }
-
-            float T = 1.0f;
-            if (dt > 0.0f) {
-#if LF_PRE_PACKED
-                // blobs in pairs: y, y^2, the exponent, the density sum and the
-                // per-blob weights in packed FP32 pairs
-                constexpr int BP = BMAX / 2;
-                float2 Y0[BP], DY[BP], LA[BP], G2[BP];
-#pragma unroll
-                for (int q = 0; q < BP; ++q) {
-                    Y0[q] = make_float2(y0[2 * q], y0[2 * q + 1]);
-                    DY[q] = make_float2(dy0[2 * q], dy0[2 * q + 1]);
-                    LA[q] = make_float2(la[2 * q], la[2 * q + 1]);
-                    G2[q] = make_float2(0.0f, 0.0f);
-                }
-                float kf = 0.0f;
-#pragma unroll kPreStepUnroll
-                for (uint32_t st = 0; st < p.steps; ++st, kf += 1.0f) {
-                    const float2 kf2 = make_float2(kf, kf);
-                    float2 g2[BP], sig2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-                    for (int q = 0; q < BP; ++q) {
-                        const float2 y = fma2(kf2, DY[q], Y0[q]);
-                        const float2 arg = sub2(LA[q], mul2(y, y));
-                        g2[q] = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
-                        sig2 = add2(sig2, g2[q]);
-                    }
-                    // step of constant density: weight T (1 - e^-x) / sigma = T dt (1 - e^-x) / x
-                    const float xs = (sig2.x + sig2.y) * dt;
-                    const float E = ex2_approx(-xs * kLog2e);
-                    const float w = T * one_minus_exp_over_x(xs, E) * dt;
-                    const float2 w2 = make_float2(w, w);
-#pragma unroll
-                    for (int q = 0; q < BP; ++q) G2[q] = fma2(w2, g2[q], G2[q]);
-                    T *= E;
-                }
-#pragma unroll
-                for (int q = 0; q < BP; ++q) {
-                    G[2 * q] = G2[q].x;
-                    G[2 * q + 1] = G2[q].y;
-                }
-#else
-                float kf = 0.0f;
-#pragma unroll kPreStepUnroll
-                for (uint32_t st = 0; st < p.steps; ++st, kf += 1.0f) {
-                    float g[BMAX], sig = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < BMAX; ++k) {
-                        const float y = fmaf(kf, dy0[k], y0[k]);
-                        g[k] = ex2_approx(fmaf(-y, y, la[k]));
-                        sig += g[k];
-                    }
-                    // step of constant density: weight T (1 - e^-x) / sigma = T dt (1 - e^-x) / x
-                    const float xs = sig * dt;
-                    const float E = ex2_approx(-xs * kLog2e);
-                    const float w = T * one_minus_exp_over_x(xs, E) * dt;
-#pragma unroll
-                    for (int k = 0; k < BMAX; ++k) G[k] = fmaf(w, g[k], G[k]);
-                    T *= E;
-                }
-#endif
-            }
-            float L0 = 0.0f, L1 = 0.0f, L2 = 0.0f;
-#pragma unroll
-            for (int k = 0; k < BMAX; ++k) {
-                const float4 bc = p.blob_col[k];
-                L0 = fmaf(G[k], bc.x, L0);
-                L1 = fmaf(G[k], bc.y, L1);
-                L2 = fmaf(G[k], bc.z, L2);
-            }
-            acc0 += fmaf(T, fmaf(p.bg1[0], bgw, p.bg0[0]), L0);
-            acc1 += fmaf(T, fmaf(p.bg1[1], bgw, p.bg0[1]), L1);
-            acc2 += fmaf(T, fmaf(p.bg1[2], bgw, p.bg0[2]), L2);
-            acc3 += 1.0f - T;
+            const float4 r = march<BMAX>(p, ox, oy, oz, dx, dy, dz, t_end);
+            acc0 += r.x;
+            acc1 += r.y;
+            acc2 += r.z;
+            acc3 += r.w;
         }
         const float inv = 1.0f / (float)p.spp;
         if (p.C == 4) {
@@ -249,6 +263,61 @@ __global__ void __launch_bounds__(256, BMAX <= 8 ? LF_PRE_MIN_BLOCKS : 1)
             o[2] = acc2 * inv;
         }
     }
+}
+
+// Direct render of the same volume, one thread per pixel of one view: the
+// pixel's camera ray and its front hit h_o on S (the FP32 steps of the
+// light-field render), the far end of the ray inside S from h_o in FP64 (the
+// FP32 form of |h_o - O|^2 - R^2 cancels for grazing rays), then the
+// integral of the precompute along that ray (one sample, no jitter). Misses
+// store 0.
+template <int BMAX>
+__global__ void __launch_bounds__(256, BMAX <= 8 ? LF_PRE_MIN_BLOCKS : 1)
+    volume_direct_kernel(const __grid_constant__ PrecomputeParams p, const __grid_constant__ ViewK v,
+                         const __grid_constant__ SphereK S, double R)
+{
+    const uint64_t total = (uint64_t)v.width * v.height;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const uint32_t y = (uint32_t)(t / v.width), x = (uint32_t)(t - (uint64_t)y * v.width);
+        const float3 d = camera_dir(v, x, y);
+        float3 ho, hd;
+        float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (intersect_sphere(S, v.eye, d, ho, hd)) {
+            const double f0 = __dsub_rn((double)ho.x, S.o64[0]);
+            const double f1 = __dsub_rn((double)ho.y, S.o64[1]);
+            const double f2 = __dsub_rn((double)ho.z, S.o64[2]);
+            const double b = __dadd_rn(__dadd_rn(__dmul_rn(f0, (double)d.x), __dmul_rn(f1, (double)d.y)),
+                                       __dmul_rn(f2, (double)d.z));
+            const double c = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(f0, f0), __dmul_rn(f1, f1)), __dmul_rn(f2, f2)),
+                                       __dmul_rn(R, R));
+            const double disc = __dsub_rn(__dmul_rn(b, b), c);
+            const double te = disc > 0.0 ? __dadd_rn(-b, __dsqrt_rn(disc)) : 0.0;
+            r = march<BMAX>(p, ho.x, ho.y, ho.z, d.x, d.y, d.z, te > 0.0 ? (float)te : 0.0f);
+        }
+        const uint64_t pix = v.out_offset + t;
+        if (p.C == 4) {
+            reinterpret_cast<float4 *>(p.out)[pix] = r;
+        } else {
+            float *o = p.out + 3 * pix;
+            o[0] = r.x;
+            o[1] = r.y;
+            o[2] = r.z;
+        }
+    }
+}
+
+cudaError_t launch_volume_direct(const PrecomputeParams &p, const ViewK &v, const SphereK &S, double R,
+                                 cudaStream_t st)
+{
+    const uint64_t total = (uint64_t)v.width * v.height;
+    const uint64_t blocks = (total + 255) / 256;
+    const unsigned grid = (unsigned)(blocks < (1ull << 20) ? blocks : (1ull << 20));
+    if (p.nb <= 8)
+        volume_direct_kernel<8><<<grid, 256, 0, st>>>(p, v, S, R);
+    else
+        volume_direct_kernel<kMaxBlobs><<<grid, 256, 0, st>>>(p, v, S, R);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_precompute(const PrecomputeParams &p, cudaStream_t st)

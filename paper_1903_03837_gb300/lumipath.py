@@ -101,6 +101,8 @@ def lib():
                 "lf_render_noalloc": (st, [C.POINTER(lf_table_desc), vp, vp, C.POINTER(lf_view), u32,
                                            C.POINTER(lf_launch), vp, vp, vp]),
                 "lf_precompute_table": (st, [C.POINTER(lf_precompute_desc), C.POINTER(lf_blob), vp, vp]),
+                "lf_render_volume": (st, [C.POINTER(lf_precompute_desc), C.POINTER(lf_blob),
+                                          C.POINTER(lf_view), u32, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -221,8 +223,15 @@ def lf_render_noalloc(desc: lf_table_desc, radiance_ptr: int, scales_ptr: Option
 
 
 def lf_precompute_table(desc: lf_precompute_desc, blobs, out_ptr: int, stream: int = 0):
-    """Light-field precompute of a volume scene into a device FP32 table (Section 3)."""
+    """Light-field precompute of a volume scene into a device FP32 table (Section 2)."""
     _check(lib().lf_precompute_table(C.byref(desc), blobs, C.c_void_p(out_ptr), C.c_void_p(stream or None)))
+
+
+def lf_render_volume(desc: lf_precompute_desc, blobs, views, n_views: int, out_ptr: int, stream: int = 0):
+    """Direct render of the precompute's volume along each pixel's ray (the
+    ground truth of a light-field render of the precomputed table)."""
+    _check(lib().lf_render_volume(C.byref(desc), blobs, views, n_views, C.c_void_p(out_ptr),
+                                  C.c_void_p(stream or None)))
 
 
 def lf_device_sm_count() -> int:

@@ -6,8 +6,9 @@ current CUDA stream; the kernels of liblumipath.so do all of the work.
 * ``RenderFunction``: ``torch.autograd.Function`` whose backward is the
   library's scatter-add kernel, fed with the forward's indices (for fitting a
   table to target views); ``fit_step``: one data-parallel fitting step
-* ``precompute_table``: the light-field precompute of Section 3 (rays r_k with
-  jittered origins through an analytic volume), on the GPU
+* ``precompute_table``: the light-field precompute of Section 2 (rays r_k with
+  jittered origins through an analytic volume), on the GPU; ``render_volume``:
+  the direct render of that volume along each pixel's ray (ground truth)
 * ``fill_lobe_table``: the synthetic lobe radiance field, filled on the GPU
 * ``quantize_table``: per-row FP16 / E4M3 storage of an FP32 table
 """
@@ -219,17 +220,10 @@ def fill_lobe_table(lobes, M: int, N: int, out: Optional[torch.Tensor] = None) -
     return out
 
 
-def precompute_table(volume, M: int, N: int, C: int = 4, rows: Optional[int] = None,
-                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """FP32 [rows, N, C] light field of an emission-absorption volume scene
-    (Section 3: rays r_k with jittered origins; `volume` as lf_inputs.Volume:
-    mu, width, dens, emit, bg0, bg1, spp, steps, jitter, seed, R, O)."""
-    rows = M if rows is None else int(rows)
-    if out is None:
-        out = torch.empty((rows, N, C), dtype=torch.float32, device="cuda")
-    _need_cuda(out, "out")
-    if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != rows * N * C:
-        raise ValueError("out must be a contiguous float32 tensor of rows * N * C elements")
+def _volume_desc(volume, M: int, N: int, C: int, rows: int):
+    """lf_precompute_desc and lf_blob array of a volume scene (`volume` as
+    lf_inputs.Volume: mu, width, dens, emit, bg0, bg1, spp, steps, jitter,
+    seed, R, O)."""
     B = len(volume.width)
     if B > lp.LF_PRECOMPUTE_MAX_BLOBS:
         raise ValueError(f"at most {lp.LF_PRECOMPUTE_MAX_BLOBS} blobs")
@@ -247,7 +241,38 @@ def precompute_table(volume, M: int, N: int, C: int = 4, rows: Optional[int] = N
     d.seed = int(volume.seed) & (2**64 - 1)
     d.bg0[:] = [float(x) for x in volume.bg0]
     d.bg1[:] = [float(x) for x in volume.bg1]
+    return d, blobs
+
+
+def precompute_table(volume, M: int, N: int, C: int = 4, rows: Optional[int] = None,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """FP32 [rows, N, C] light field of an emission-absorption volume scene
+    (Section 2: rays r_k with jittered origins; `volume` as lf_inputs.Volume:
+    mu, width, dens, emit, bg0, bg1, spp, steps, jitter, seed, R, O)."""
+    rows = M if rows is None else int(rows)
+    if out is None:
+        out = torch.empty((rows, N, C), dtype=torch.float32, device="cuda")
+    _need_cuda(out, "out")
+    if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != rows * N * C:
+        raise ValueError("out must be a contiguous float32 tensor of rows * N * C elements")
+    d, blobs = _volume_desc(volume, M, N, C, rows)
     lp.lf_precompute_table(d, blobs, out.data_ptr(), _stream())
+    return out
+
+
+def render_volume(volume, views: Sequence, C: int = 4, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Direct render [P, C] float32 of a volume scene along each pixel's ray
+    (front hit on S to the far intersection, `volume.steps` midpoint steps, one
+    sample): the ground truth of a light-field render of its precomputed table.
+    Misses are 0."""
+    P = total_pixels(views)
+    if out is None:
+        out = torch.empty((P, C), dtype=torch.float32, device="cuda")
+    _need_cuda(out, "out")
+    if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() < P * C:
+        raise ValueError("out must be a contiguous float32 tensor of at least P * C elements")
+    d, blobs = _volume_desc(volume, 1, 1, C, 1)
+    lp.lf_render_volume(d, blobs, lp.make_views(views), len(views), out.data_ptr(), _stream())
     return out
 
 

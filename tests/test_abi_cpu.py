@@ -185,3 +185,39 @@ def test_borrowed_table_must_be_aligned_for_its_vector_loads(dtype, Cc, ptr):
     assert s == lp.LF_ERR_INVALID_ARG, lp.lf_last_error()
     assert "aligned" in lp.lf_last_error()
     assert handle.value is None
+
+
+def _one_view():
+    import lf_inputs
+    return lp.make_views([lf_inputs.look_at((2.5, 0.3, 0.2), (0, 0, 0), 8, 8)])
+
+
+@pytest.mark.parametrize("kw,blob", [
+    (dict(radius=0.0), {}), (dict(radius=float("nan")), {}), (dict(C=5), {}), (dict(steps=0), {}),
+    (dict(steps=5000), {}), (dict(nb=17), {}), (dict(bg0=[float("nan"), 0.0, 0.0]), {}),
+    ({}, dict(width=0.0)), ({}, dict(density=-1.0)),
+])
+def test_render_volume_rejects_bad_volumes(kw, blob):
+    # the direct render shares the precompute's volume checks; all before any CUDA call
+    L = lp.lib()
+    d = _pdesc(**kw)
+    st = L.lf_render_volume(C.byref(d), _blobs(n=max(1, d.n_blobs), **blob), _one_view(), 1,
+                            C.c_void_p(4096), None)
+    assert st == lp.LF_ERR_INVALID_ARG, (kw, blob, lp.lf_last_error())
+
+
+def test_render_volume_checks_views_and_output_not_the_sets():
+    L = lp.lib()
+    # the SF-set fields are not used: M = 0, rows = 0, spp = 0 and jitter = 2 pass the
+    # volume checks, and the call stops at the (empty) view list instead
+    d = _pdesc(M=0, rows=0, spp=0, jitter=2)
+    assert L.lf_render_volume(C.byref(d), _blobs(), _one_view(), 0, C.c_void_p(4096), None) == \
+        lp.LF_ERR_INVALID_ARG
+    assert "n_views" in lp.lf_last_error()
+    d = _pdesc()
+    assert L.lf_render_volume(None, _blobs(), _one_view(), 1, C.c_void_p(4096), None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_render_volume(C.byref(d), _blobs(), None, 1, C.c_void_p(4096), None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_render_volume(C.byref(d), _blobs(), _one_view(), 1, None, None) == lp.LF_ERR_INVALID_ARG
+    assert L.lf_render_volume(C.byref(d), _blobs(), _one_view(), 1, C.c_void_p(4100), None) == \
+        lp.LF_ERR_INVALID_ARG
+    assert "aligned" in lp.lf_last_error()

@@ -1,4 +1,4 @@
-"""GPU parity of the light-field precompute (Section 3) against the CPU oracle,
+"""GPU parity of the light-field precompute (Section 2) against the CPU oracle,
 called through the C ABI (lf_precompute_table).
 
 Bar: |GPU - oracle| <= 1e-5 + steps * 2^-21 * (1 + |oracle|) per channel. The
@@ -149,3 +149,70 @@ def test_upper_hemisphere_precompute_renders_like_the_oracle(api):
     err = np.abs(out.cpu().numpy() - o_out)
     assert err.max() <= 1e-5 + vol.steps * 2.0 ** -21 * 2.0 + 1e-6, float(err.max())
     lf.close()
+
+
+# --------------------------------------------------------------------------
+# Direct render of the volume (lf_render_volume): the ground truth of a
+# light-field render of the precomputed table
+# --------------------------------------------------------------------------
+def direct_views():
+    return lf_inputs.pack_offsets([lf_inputs.look_at((2.2, -1.1, 0.9), (0, 0, 0), 64, 48),
+                                   lf_inputs.look_at((0.05, 0.02, 2.6), (0, 0, 0), 40, 40),      # over a pole
+                                   lf_inputs.look_at((0.3, 0.2, 0.1), (0, 0, 0), 24, 24),        # eye inside S
+                                   lf_inputs.look_at((-3.5, 0.4, -0.2), (0, 0.3, 0), 33, 17)])   # ragged size
+
+
+@pytest.mark.parametrize("case", ["rgba", "rgb", "sixteen_blobs", "moved_sphere", "empty", "one_step",
+                                  "many_steps"])
+def test_direct_render_matches_oracle(api, case):
+    kw = dict(B=8, spp=1, steps=32)
+    C = 4
+    if case == "sixteen_blobs":
+        kw.update(B=16)
+    if case == "moved_sphere":
+        kw.update(R=2.5, O=(0.5, -0.25, 1.0))
+    if case == "one_step":
+        kw.update(steps=1)
+    if case == "many_steps":
+        kw.update(steps=512)
+    vol = lf_inputs.draw_volume(9, **kw)
+    if case == "empty":
+        vol = lf_inputs.Volume(np.zeros((0, 3)), np.zeros(0), np.zeros(0), np.zeros((0, 3)), spp=1, steps=8)
+    if case == "rgb":
+        C = 3
+    views = direct_views()
+    if case == "moved_sphere":
+        views = lf_inputs.pack_offsets([lf_inputs.look_at(np.asarray(vol.O) + np.array([5.0, 1.0, -2.0]),
+                                                          vol.O, 64, 48)])
+    got = api.render_volume(vol, views, C)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy()
+    want, hits = oracle.volume_pixels(vol, views, lf_inputs.pixel_list(views), C)
+    assert hits > 500
+    assert np.all(got[np.all(want == 0.0, axis=1)] == 0.0)     # misses store 0
+    check(vol, got, want)
+
+
+def test_light_field_render_converges_to_the_direct_render_on_the_gpu(api):
+    # GPU precompute -> GPU light-field render, against the GPU direct render: the PSNR
+    # rises with the SF set sizes, and at the sizes the oracle can afford it equals the
+    # oracle's own PSNR of the same comparison.
+    vol = lf_inputs.draw_volume(8, B=8, spp=2, steps=32)
+    views = [lf_inputs.look_at(np.array([2.1, -1.3, 0.8]), (0, 0, 0), 96, 72)]
+    gt = api.render_volume(vol, views, 4)
+    gt_o, _ = oracle.volume_pixels(vol, views, lf_inputs.pixel_list(views))
+    psnr = []
+    for M, N in [(1024, 256), (4096, 512), (16384, 1024), (65536, 2048)]:
+        T = api.precompute_table(vol, M, N, 4)
+        lf = api.LightField(T, "f32", borrow=True)
+        out, idx = lf.render(views, with_idx=True)
+        lf.sync_status()
+        hit = idx[:, 0].cpu().numpy() >= 0
+        psnr.append(oracle.psnr(gt.cpu().numpy()[:, :3], out.cpu().numpy()[:, :3], hit))
+        if M <= 4096:
+            T_o = oracle.volume_table(vol, M, N, 4)
+            o_out, _, _ = oracle.render_views(oracle.Scene(M, N, 4, "f32", T_o), views)
+            assert abs(psnr[-1] - oracle.psnr(gt_o[:, :3], o_out[:, :3], hit)) < 0.02, psnr
+        lf.close()
+        del T
+    assert all(b > a + 2.0 for a, b in zip(psnr, psnr[1:])), psnr

@@ -1,4 +1,4 @@
-"""Pins of the light-field precompute oracle (Section 3) against facts that do
+"""Pins of the light-field precompute oracle (Section 2) against facts that do
 not come from the oracle itself: closed forms of the emission-absorption
 integral, the geometry of the ray r_k and of the jitter disk, invariances and
 the convergence order of the midpoint rule."""
@@ -183,3 +183,88 @@ def test_scale_invariance():
     tex = np.array([[3, 5], [64, 60], [100, 1], [127, 33]])
     np.testing.assert_allclose(oracle.volume_table(big, M, N, 4, texels=tex),
                                oracle.volume_table(base, M, N, 4, texels=tex), rtol=1e-10, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Direct render of the volume (the ground truth of a light-field render)
+# --------------------------------------------------------------------------
+def _views():
+    return lf_inputs.pack_offsets([lf_inputs.look_at((2.5, 0.3, 0.2), (0, 0, 0), 40, 30),
+                                   lf_inputs.look_at((0.2, -0.1, -3.0), (0.1, 0, 0), 24, 24)])
+
+
+def test_direct_pixels_of_an_empty_volume_are_the_background():
+    v = vol(np.zeros((0, 3)), [], [], np.zeros((0, 3)))
+    views = _views()
+    pix = lf_inputs.pixel_list(views)
+    out, hits = oracle.volume_pixels(v, views, pix)
+    n_hit = 0
+    for k, (vi, x, y) in enumerate(pix):
+        hit, d, _, _, _, _ = oracle.trace_pixel(1.0, (0, 0, 0), views[vi], x, y)
+        if hit:
+            n_hit += 1
+            np.testing.assert_allclose(out[k, :3], bg(v, d.astype(float)), rtol=0, atol=1e-15)
+            assert out[k, 3] == 0.0
+        else:
+            assert np.all(out[k] == 0.0)
+    assert hits == n_hit > 100
+
+
+def test_direct_pixel_single_blob_closed_form():
+    # The pixel's ray enters S at h_o and leaves at h_d: tau from the erf closed form
+    # over [0, |h_d - h_o|] (the FP32 hits are within ~1e-7 of the exact chord ends).
+    mu = np.array([0.1, -0.2, 0.15])
+    e = np.array([0.9, 0.4, 0.2])
+    v = vol([mu], [0.2], [5.0], [e], steps=20000)
+    views = _views()
+    pix = lf_inputs.pixel_list(views, stride=7)
+    out, hits = oracle.volume_pixels(v, views, pix)
+    checked = 0
+    for k, (vi, x, y) in enumerate(pix):
+        hit, d, ho, hd, _, _ = oracle.trace_pixel(1.0, (0, 0, 0), views[vi], x, y)
+        if not hit:
+            continue
+        d = d.astype(float)
+        tau = gauss_depth(ho.astype(float), d, float(np.linalg.norm(hd.astype(float) - ho)), mu, 0.2, 5.0)
+        want = e * (1 - math.exp(-tau)) + math.exp(-tau) * bg(v, d)
+        np.testing.assert_allclose(out[k, :3], want, rtol=0, atol=2e-6)
+        assert abs(out[k, 3] - (1 - math.exp(-tau))) < 2e-6
+        checked += 1
+    assert checked > 20
+
+
+def test_direct_pixel_along_a_chord_equals_the_unjittered_texel():
+    # A single-pixel view aimed from outside S through O + R p_i at O + R p_j sees the
+    # ray r_k of texel (i, j) without jitter: the same radiance up to the FP32 rounding
+    # of its front hit.
+    v = lf_inputs.draw_volume(4, B=6, spp=1, steps=48)
+    v.jitter = 0
+    M, N = 300, 120
+    rng = np.random.default_rng(3)
+    pairs = [(int(rng.integers(M)), int(rng.integers(N))) for _ in range(60)]
+    views = []
+    for i, j in pairs:
+        p, q, d = chord(M, N, i, j)
+        views.append(lf_inputs.look_at(p - rng.uniform(0.3, 2.0) * d, q, 1, 1))
+    views = lf_inputs.pack_offsets(views)
+    out, hits = oracle.volume_pixels(v, views, lf_inputs.pixel_list(views))
+    want = oracle.volume_table(v, M, N, 4, texels=np.array(pairs))
+    assert hits == len(pairs)
+    np.testing.assert_allclose(out, want, rtol=0, atol=3e-6)
+
+
+def test_light_field_render_converges_to_the_direct_render():
+    # The light-field render of the precomputed table approaches the direct render of
+    # the volume as the SF sets grow (Section 2: the table samples the rays between the
+    # two point sets; the filter blends the nearest ones): PSNR rises with M and N.
+    v = lf_inputs.draw_volume(8, B=8, spp=2, steps=32)
+    views = [lf_inputs.look_at(np.array([2.1, -1.3, 0.8]), (0, 0, 0), 96, 72)]
+    gt, hits = oracle.volume_pixels(v, views, lf_inputs.pixel_list(views))
+    psnr = []
+    for M, N in [(256, 64), (1024, 256), (4096, 512)]:
+        T = oracle.volume_table(v, M, N, 4)
+        out, idx, _ = oracle.render_views(oracle.Scene(M, N, 4, "f32", T), views)
+        hit = idx[:, 0] >= 0
+        assert hit.sum() == hits > 3000
+        psnr.append(oracle.psnr(gt[:, :3], out[:, :3], hit))
+    assert psnr[0] > 25 and psnr[1] > psnr[0] + 4 and psnr[2] > psnr[1] + 4, psnr
