@@ -300,6 +300,13 @@ void fill_sphere_consts(SphereK &S, double R, const double O[3])
     S.r2_l = (float)(r2 - (double)S.r2_h);
     S.inv_r2 = (float)(1.0 / r2);
     S.centred = (O[0] == 0.0 && O[1] == 0.0 && O[2] == 0.0) ? 1u : 0u;
+    S.r32 = (float)R;
+    for (int k = 0; k < 3; ++k) {
+        S.o32[k] = (float)O[k];
+        S.o_hi[k] = (float)O[k];
+        S.o_lo[k] = (float)(O[k] - (double)S.o_hi[k]);
+        S.o64[k] = O[k];
+    }
 }
 }  // namespace lfk
 
@@ -421,13 +428,6 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
 
     lfk::SphereK &S = t->sphere;
     lfk::fill_sphere_consts(S, d->radius, d->center);
-    S.r32 = (float)d->radius;
-    for (int k = 0; k < 3; ++k) {
-        S.o32[k] = (float)d->center[k];
-        S.o_hi[k] = (float)d->center[k];
-        S.o_lo[k] = (float)(d->center[k] - (double)S.o_hi[k]);
-        S.o64[k] = d->center[k];
-    }
     const double four_pi = 12.566370614359172953850573533118;
     t->po = {t->points, t->points + M, M, (float)M, (float)(1.0 / std::sqrt(four_pi / (double)M))};
     t->pd = {t->points + 2 * (uint64_t)M, t->points + 2 * (uint64_t)M + N, N, (float)N,
@@ -627,7 +627,7 @@ lf_status lf_render_volume(const lf_precompute_desc *d, const lf_blob *blobs, co
     if (s != LF_OK) return s;
     s = check_views(views, n_views);
     if (s != LF_OK) return s;
-    lfk::SphereK S;
+    lfk::SphereK S{};
     lfk::fill_sphere_consts(S, d->radius, d->center);
     cudaStream_t st = (cudaStream_t)stream;
     for (uint32_t v = 0; v < n_views; ++v) {

@@ -97,8 +97,10 @@ cudaError_t launch_volume_direct(const PrecomputeParams &p, const ViewK &v, cons
 // Fills the conservative-miss constants of a view for sphere (R, O) (lf_abi.cu).
 void fill_view_miss_consts(ViewK &k, double R, const double O[3]);
 
-// Host-side constants of the sphere used by the unit-hit step: 1/R and R^2 as
-// hi/lo float pairs, 1/R^2, and whether O is the origin (lf_abi.cu).
+// Host-side constants of sphere S (lf_abi.cu): FP32 radius and centre for the
+// ray/sphere step, the centre as a hi/lo float pair and in FP64, and for the
+// unit-hit step 1/R and R^2 as hi/lo float pairs, 1/R^2 and whether O is the
+// origin.
 void fill_sphere_consts(SphereK &S, double R, const double O[3]);
 
 // Sets the calling thread's lf_last_error() message (lf_abi.cu).

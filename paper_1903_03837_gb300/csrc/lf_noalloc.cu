@@ -201,13 +201,6 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
     lfk::RenderParamsBase b;
     memset(&b, 0, sizeof b);
     lfk::fill_sphere_consts(b.sphere, d->radius, d->center);
-    b.sphere.r32 = (float)d->radius;
-    for (int k = 0; k < 3; ++k) {
-        b.sphere.o32[k] = (float)d->center[k];
-        b.sphere.o_hi[k] = (float)d->center[k];
-        b.sphere.o_lo[k] = (float)(d->center[k] - (double)b.sphere.o_hi[k]);
-        b.sphere.o64[k] = d->center[k];
-    }
     const double four_pi = 12.566370614359172953850573533118;
     b.po = {po_hi, po_lo, M, (float)M, (float)(1.0 / std::sqrt(four_pi / (double)M))};
     b.pd = {pd_hi, pd_lo, N, (float)N, (float)(1.0 / std::sqrt(four_pi / (double)N))};
