@@ -89,6 +89,12 @@ def recorded_counter(dtype: str, name: str):
     return int(v) if v else None
 
 
+def recorded_pct(dtype: str, name: str):
+    """A recorded percentage of peak (ncu, the capture's own launch time), or None."""
+    v = _recorded().get(f"{dtype}_{name}")
+    return float(v) if v else None
+
+
 def recorded_traffic(dtype: str):
     """DRAM bytes (read + write) per launch, or None (see _recorded)."""
     return recorded_counter(dtype, "dram_bytes_per_launch")
@@ -419,6 +425,8 @@ def run_ours(args, rank: int, world: int):
                      "l2_bytes_per_launch": recorded_counter(args.dtype, "l2_bytes_per_launch"),
                      "l2_achieved_gbs": (recorded_counter(args.dtype, "l2_bytes_per_launch") or 0) / avg_launch_s / 1e9
                      or None,
+                     "l2_pct_of_peak_ncu": recorded_pct(args.dtype, "l2_pct_of_peak"),
+                     "dram_pct_of_peak_ncu": recorded_pct(args.dtype, "dram_pct_of_peak"),
                      "issue": issue_roofline(args.dtype, avg_launch_s)},
         "clocks": clocks,
         "e2e": {"value": world * args.steps * rays / e2e_s / 1e9, "unit": UNIT,
