@@ -292,9 +292,13 @@ def run_ours(args, rank: int, world: int):
     for dt in (("f16", "f32") if not args.no_variants else ()):
         if dt == args.dtype:
             continue
+        # each table type at its own best launch shape (the 16-byte FP32 texels
+        # favour narrower warp tiles than the 4-byte E4M3 ones)
+        vlaunch = launch if args.launch else autotune.best_launch(
+            tables[dt], [frame_views[my_frames[0]]], key=f"{args.workload}-{dt}", quick=args.quick_tune)
         tm, pm, nb = timed(dt)
         variants[dt] = {"grays_s": world * args.steps * rays / (tm * 1e-3) / 1e9,
-                        "ms_per_step": tm / args.steps,
+                        "ms_per_step": tm / args.steps, "launch": vlaunch,
                         "hbm_frac_of_measured": nb / (sum(pm) * 1e-3) / 1e9 / measured_peaks()[0]}
 
     # quality of the quantised tables against the FP32-table image (full frame, GPU)

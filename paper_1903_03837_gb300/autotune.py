@@ -22,7 +22,7 @@ CANDIDATES = [
     (16, 16, 8, 0, 0), (16, 16, 8, 1, 0), (16, 16, 8, 0, 1), (16, 16, 8, 1, 1),
     (32, 8, 8, 0, 0), (32, 8, 8, 1, 1), (8, 32, 8, 0, 0), (16, 8, 8, 0, 0),
     (16, 16, 16, 0, 0), (32, 8, 32, 0, 0), (16, 16, 4, 0, 0), (64, 4, 8, 1, 1),
-    (32, 4, 8, 0, 0), (8, 16, 8, 1, 1),
+    (32, 4, 8, 0, 0), (8, 16, 8, 1, 1), (16, 8, 4, 0, 0),
 ]
 QUICK = [(16, 16, 8, 0, 0), (16, 16, 8, 1, 1), (32, 8, 8, 0, 0), (16, 8, 8, 0, 0)]
 
