@@ -573,9 +573,16 @@ def light_field_vs_direct(args, vol, views, table):
         _, idx = lf.render(views, out=img, with_idx=True)
         hit = idx[:, 0].cpu().numpy() >= 0
         ms = timed(lambda: lf.render(views, out=img))
+        img_np = img.cpu().numpy()
+        ssim = [ssim_mean(gt_np[v.out_offset:v.out_offset + v.pixels, :3].reshape(v.height, v.width, 3),
+                          img_np[v.out_offset:v.out_offset + v.pixels, :3].reshape(v.height, v.width, 3),
+                          hit[v.out_offset:v.out_offset + v.pixels].reshape(v.height, v.width),
+                          float(gt_np[hit, :3].max()))
+                for v in views]
         res["tables"][f"{M:,} x {N:,}"] = {
             "light_field_ms": ms, "light_field_grays_s": rays / (ms * 1e-3) / 1e9,
-            "psnr_vs_direct_db": psnr_db(gt_np[:, :3], img.cpu().numpy()[:, :3], hit),
+            "psnr_vs_direct_db": psnr_db(gt_np[:, :3], img_np[:, :3], hit),
+            "ssim_vs_direct": float(np.mean(ssim)),
             "hit_fraction": float(hit.mean())}
         lf.close()
         del T
@@ -588,6 +595,28 @@ def psnr_db(ref, test, hit):
     t = np.asarray(test, np.float64)[hit]
     mse = float(np.mean((r - t) ** 2))
     return float("inf") if mse == 0.0 else 10.0 * math.log10(float(r.max()) ** 2 / mse)
+
+
+def ssim_mean(ref, img, mask, data_range):
+    """Mean structural similarity (Wang et al., 2004: Gaussian window of standard
+    deviation 1.5 truncated to 11 x 11, C1 = (0.01 L)^2, C2 = (0.03 L)^2) of one
+    view's image [H, W, C] against the reference, averaged over the channels and
+    over the pixels of `mask` [H, W] -- the quality measure the paper reports
+    against its path-traced ground truth (Section 3)."""
+    from scipy.ndimage import gaussian_filter
+    x = np.asarray(ref, np.float64)
+    y = np.asarray(img, np.float64)
+    c1, c2 = (0.01 * data_range) ** 2, (0.03 * data_range) ** 2
+    g = lambda a: gaussian_filter(a, sigma=1.5, truncate=3.5, mode="nearest")
+    maps = []
+    for c in range(x.shape[2]):
+        a, b = x[:, :, c], y[:, :, c]
+        mx, my = g(a), g(b)
+        vx = g(a * a) - mx * mx
+        vy = g(b * b) - my * my
+        cxy = g(a * b) - mx * my
+        maps.append(((2 * mx * my + c1) * (2 * cxy + c2)) / ((mx * mx + my * my + c1) * (vx + vy + c2)))
+    return float(np.mean(np.mean(maps, axis=0)[mask]))
 
 
 def run_fit_steps(args):
