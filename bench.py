@@ -461,6 +461,8 @@ def run_ours(args, rank: int, world: int):
         line["batching"] = run_batching(args)
         torch.cuda.empty_cache()
         line["precompute"] = run_precompute(args)
+        torch.cuda.empty_cache()
+        line["post_filter"] = run_post_filter(args)
         tables = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "large":
         line["cpu_baseline"], psnr64, psnr_k = cpu_baseline(cfg, frame_views[f0], gpu_images, args, k_images)
@@ -595,6 +597,87 @@ def psnr_db(ref, test, hit):
     t = np.asarray(test, np.float64)[hit]
     mse = float(np.mean((r - t) ** 2))
     return float("inf") if mse == 0.0 else 10.0 * math.log10(float(r.max()) ** 2 / mse)
+
+
+def run_post_filter(args):
+    """Learned post-filter (Section 2, post-processing; the generator's loss,
+    no adversary): trained on the light-field renders of 40 volume scenes'
+    1,024 x 256 tables against their direct renders, then measured on 8
+    held-out scenes (4 views of 256x256 each): PSNR and SSIM against the direct
+    render before and after the filter (lf_post_filter), next to a 16x larger
+    table without it, and the filter's time per frame next to the render's."""
+    import torch
+    from paper_1903_03837_gb300 import torch_api as api, post_filter as pf
+    cfg = lf_inputs.config_post_filter()
+    M, N = cfg.M, cfg.N
+    t0 = time.time()
+    feats, targets, _ = pf.make_pairs(cfg.extra["train"], M, N)
+    t1 = time.time()
+    steps = 2000
+    w, hist = pf.train(feats, targets, steps=steps, batch=16)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    del feats, targets
+    st = torch.cuda.current_stream()
+    reps = max(3, min(args.steps, 10))
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    rows = {"light_field": [], "filtered": [], "light_field_16x": []}
+    ssims = {k: [] for k in rows}
+    filt_ms = render_ms = 0.0
+    rays = 0
+    for vol, views in cfg.extra["test"]:
+        gt = api.render_volume(vol, views, 4)
+        gt_np = gt.cpu().numpy()
+        out = {}
+        for key, (m, n) in (("light_field", (M, N)), ("light_field_16x", (4 * M, 4 * N))):
+            T = api.precompute_table(vol, m, n, 4)
+            lf = api.LightField(T, "f32", borrow=True)
+            img, idx = lf.render(views, with_idx=True)
+            if key == "light_field":
+                render_ms += timed(lambda: lf.render(views, out=img))
+                filtered = pf.apply(w, views, img)
+                filt_ms += timed(lambda: pf.apply(w, views, img, out=filtered))
+                out["filtered"] = filtered.cpu().numpy()
+                hit = idx[:, 0].cpu().numpy() >= 0
+            out[key] = img.cpu().numpy()
+            lf.close()
+            del T
+        rays += lf_inputs.total_pixels(views)
+        peak = float(gt_np[hit, :3].max())
+        for key, im in out.items():
+            rows[key].append((gt_np[hit, :3], im[hit, :3], peak))
+            for v in views:
+                a, b = v.out_offset, v.out_offset + v.pixels
+                ssims[key].append(ssim_mean(gt_np[a:b, :3].reshape(v.height, v.width, 3),
+                                            im[a:b, :3].reshape(v.height, v.width, 3),
+                                            hit[a:b].reshape(v.height, v.width), peak))
+
+    def psnr_all(rs):
+        mse = np.mean(np.concatenate([((r - t) ** 2).ravel() for r, t, _ in rs]))
+        peak = max(p for _, _, p in rs)
+        return 10.0 * math.log10(peak * peak / mse)
+    n_scenes = len(cfg.extra["test"])
+    return {"workload": f"post-filter: trained on {len(cfg.extra['train'])} volume scenes x 8 views 128x128, "
+                        f"tested on {n_scenes} held-out scenes x 4 views 256x256; {M:,} x {N:,} RGBA FP32 tables",
+            "train_steps": steps, "train_s": round(t2 - t1, 2), "data_s": round(t1 - t0, 2),
+            "loss_first_last": [hist[0], hist[-1]],
+            "psnr_vs_direct_db": {k: psnr_all(v) for k, v in rows.items()},
+            "ssim_vs_direct": {k: float(np.mean(v)) for k, v in ssims.items()},
+            "filter_ms_per_scene": filt_ms / n_scenes, "render_ms_per_scene": render_ms / n_scenes,
+            "filter_gpixels_s": rays / (filt_ms * 1e-3) / 1e9,
+            "kernel": "lfk::post_filter_kernel (FP32, CUDA cores)"}
 
 
 def ssim_mean(ref, img, mask, data_range):
@@ -875,10 +958,12 @@ def main():
     ap.add_argument("--quick-tune", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--launch", default="", help="tile_w,tile_h,warp_w,order,persistent (skips the autotuner)")
-    ap.add_argument("--workload", default="large", choices=["large", "precision", "fit", "precompute"],
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "precision", "fit", "precompute", "post_filter"],
                     help="precision: 65,536 x 1,024 table, one 1920x1080 view (small profiling case); "
                          "fit: the differentiation leg alone (forward + backward + Adam per step); "
-                         "precompute: the light-field precompute leg alone")
+                         "precompute: the light-field precompute leg alone; "
+                         "post_filter: the learned post-filter leg alone")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -893,10 +978,11 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("fit", "precompute"):
-        # the fit leg (data-parallel over the ranks) or the precompute leg alone
-        # (profiling cases of the backward and precompute kernels): one JSON object
-        leg = run_fit_steps(args) if args.workload == "fit" else run_precompute(args)
+    if args.workload in ("fit", "precompute", "post_filter"):
+        # the fit leg (data-parallel over the ranks), the precompute or the
+        # post-filter leg alone (profiling cases of those kernels): one JSON object
+        leg = {"fit": run_fit_steps, "precompute": run_precompute,
+               "post_filter": run_post_filter}[args.workload](args)
         if rank == 0:
             print(json.dumps({args.workload: leg}), flush=True)
         if world > 1:

@@ -262,6 +262,26 @@ def config_precompute(seed: int = 0) -> Config:
                   extra={"volume": draw_volume(seed, B=8)})
 
 
+def config_post_filter(seed: int = 0, n_train: int = 40, n_test: int = 8) -> Config:
+    """Learned post-filter: n_train training and n_test held-out volume scenes
+    (draw_volume with 8 blobs, 2 jittered samples per texel, 32 midpoint steps;
+    seeds 100 + k and 500 + k), each with views aimed at a point within 0.2R of
+    the centre from distances U[2, 4]R: 8 views of 128x128 per training scene,
+    4 of 256x256 per held-out scene. The light field of each scene is a
+    1,024 x 256 RGBA FP32 table; its ground truth the direct render. extra:
+    "train" and "test", lists of (volume, views)."""
+    rng = np.random.default_rng(seed + 9000)
+
+    def views_of(n, size):
+        vs = [look_at(rng.uniform(2.0, 4.0) * _random_dir(rng), 0.2 * rng.uniform(0, 1) * _random_dir(rng),
+                      size, size) for _ in range(n)]
+        return pack_offsets(vs)
+    train = [(draw_volume(seed + 100 + k, B=8, spp=2, steps=32), views_of(8, 128)) for k in range(n_train)]
+    test = [(draw_volume(seed + 500 + k, B=8, spp=2, steps=32), views_of(4, 256)) for k in range(n_test)]
+    return Config("post_filter", 1024, 256, 4, 8, seed, ("f32",), test[0][1],
+                  extra={"train": train, "test": test})
+
+
 def orbit_frame(f: int, frames: int = 240, dist: float = 3.0, elev_deg: float = 20.0,
                 width: int = 3840, height: int = 2160, R: float = 1.0) -> List[View]:
     """Frame f of the orbit: centre at distance `dist`, elevation 20 degrees,

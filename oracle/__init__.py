@@ -23,6 +23,8 @@ marshals numpy arrays through ctypes. Functions:
   jittered on the disk of area A_S/M
 * ``volume_pixels``                          -- direct render of that volume along each
   pixel's ray (the ground truth of a light-field render of the precomputed table)
+* ``post_filter``, ``post_features``, ``conv3x3`` -- the learned post-filter's forward
+  (Section 2, post-processing) in FP64
 * ``psnr``                                   -- image error against an FP64 render
 
 Parity unpinned: none. Each function is pinned in ``tests/test_oracle_pins.py``.
@@ -432,6 +434,67 @@ def volume_pixels(vol, views, pix: np.ndarray, C_: int = 4, threads: Optional[in
     with ThreadPoolExecutor(nt) as ex:
         hits = sum(ex.map(work, range(len(bounds) - 1)))
     return out, int(hits)
+
+
+# --------------------------------------------------------------------------
+# Learned post-filter (Section 2, post-processing): FP64 forward of the
+# three-layer convolutional filter, from the definitions of a 3x3
+# cross-correlation with zero padding, ReLU and the residual on hit pixels
+# --------------------------------------------------------------------------
+POST_SHAPES = [(16, 4, 3, 3), (16,), (16, 16, 3, 3), (16,), (3, 16, 3, 3), (3,)]
+
+
+def post_unpack(w):
+    """(W1, b1, W2, b2, W3, b3) of the flat weight vector (FP64 copies)."""
+    w = np.asarray(w, np.float64)
+    out, k = [], 0
+    for s in POST_SHAPES:
+        n = int(np.prod(s))
+        out.append(w[k:k + n].reshape(s))
+        k += n
+    assert k == w.size
+    return out
+
+
+def conv3x3(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """out[o, y, x] = b[o] + sum_{i, dy, dx} W[o, i, dy, dx] in[i, y + dy - 1, x + dx - 1],
+    with in = 0 outside the image."""
+    I, H, Wd = x.shape
+    pad = np.zeros((I, H + 2, Wd + 2))
+    pad[:, 1:H + 1, 1:Wd + 1] = x
+    out = np.empty((W.shape[0], H, Wd))
+    for o in range(W.shape[0]):
+        acc = np.full((H, Wd), float(b[o]))
+        for i in range(I):
+            for dy in range(3):
+                for dx in range(3):
+                    acc += W[o, i, dy, dx] * pad[i, dy:dy + H, dx:dx + Wd]
+        out[o] = acc
+    return out
+
+
+def post_filter(weights, feats: np.ndarray) -> np.ndarray:
+    """The filter on one view's features [4, H, W] (R, G, B, hit): [3, H, W] =
+    (RGB + conv3(relu(conv2(relu(conv1(feats)))))) on hit pixels, 0 elsewhere."""
+    W1, b1, W2, b2, W3, b3 = post_unpack(weights)
+    x = np.asarray(feats, np.float64)
+    h = np.maximum(conv3x3(x, W1, b1), 0.0)
+    h = np.maximum(conv3x3(h, W2, b2), 0.0)
+    r = conv3x3(h, W3, b3)
+    return (x[:3] + r) * (x[3:4] != 0)
+
+
+def post_features(view, image: np.ndarray, R: float = 1.0, O=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Features [4, H, W] of one view: the RGB of its [H*W, C] image and the hit
+    mask of each pixel's ray (the FP32 ray/sphere test)."""
+    H, Wd = view.height, view.width
+    f = np.zeros((4, H, Wd))
+    img = np.asarray(image, np.float64).reshape(H, Wd, -1)
+    f[:3] = img[:, :, :3].transpose(2, 0, 1)
+    for y in range(H):
+        for x in range(Wd):
+            f[3, y, x] = 1.0 if trace_pixel(R, O, view, x, y)[0] else 0.0
+    return f
 
 
 # --------------------------------------------------------------------------

@@ -53,6 +53,7 @@ lf_status cuda_fail(cudaError_t e, const char *what)
 }
 
 bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
 lf_launch default_launch()
 {
@@ -633,6 +634,43 @@ lf_status lf_render_volume(const lf_precompute_desc *d, const lf_blob *blobs, co
     for (uint32_t v = 0; v < n_views; ++v) {
         cudaError_t e = lfk::launch_volume_direct(P, camera_of(views[v]), S, d->radius, st);
         if (e != cudaSuccess) return cuda_fail(e, "direct volume render");
+    }
+    return LF_OK;
+}
+
+lf_status lf_post_filter(double radius, const double center[3], uint32_t channels, const float *weights_dev,
+                         const lf_view *views, uint32_t n_views, const float *in_dev, float *out_dev,
+                         void *stream)
+{
+    NvtxRange nvtx_("lf_post_filter");
+    g_err.clear();
+    static_assert(lfk::kPostWeights == (int)LF_POST_WEIGHTS, "post-filter weight count");
+    if (!center || !weights_dev || !in_dev || !out_dev)
+        return fail(LF_ERR_INVALID_ARG, "center, weights, in and out must not be NULL");
+    if (!(radius > 0.0) || !std::isfinite(radius) || !finite3(center))
+        return fail(LF_ERR_INVALID_ARG, "R must be positive and finite, O finite");
+    if (channels != 3 && channels != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4");
+    if (misaligned(weights_dev, 4) || misaligned(in_dev, 4) || misaligned(out_dev, 4))
+        return fail(LF_ERR_INVALID_ARG, "weights, in and out must be 4-byte aligned");
+    lf_status s = check_views(views, n_views);
+    if (s != LF_OK) return s;
+    uint64_t P = 0;
+    for (uint32_t v = 0; v < n_views; ++v) {
+        const uint64_t end = views[v].out_offset + (uint64_t)views[v].width * views[v].height;
+        P = end > P ? end : P;
+    }
+    const uintptr_t a = (uintptr_t)in_dev, b = (uintptr_t)out_dev, bytes = (uintptr_t)(P * channels * 4);
+    if (a < b + bytes && b < a + bytes) return fail(LF_ERR_INVALID_ARG, "out must not overlap in");
+    lfk::PostParams p{};
+    lfk::fill_sphere_consts(p.sphere, radius, center);
+    p.w = weights_dev;
+    p.in = in_dev;
+    p.out = out_dev;
+    p.C = channels;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (uint32_t v = 0; v < n_views; ++v) {
+        cudaError_t e = lfk::launch_post_filter(p, camera_of(views[v]), st);
+        if (e != cudaSuccess) return cuda_fail(e, "post-filter");
     }
     return LF_OK;
 }

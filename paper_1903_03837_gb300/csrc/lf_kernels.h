@@ -94,6 +94,26 @@ cudaError_t launch_precompute(const PrecomputeParams &p, cudaStream_t st);
 cudaError_t launch_volume_direct(const PrecomputeParams &p, const ViewK &v, const SphereK &S, double R,
                                  cudaStream_t st);
 
+// lf_post.cu: the learned post-filter of the light-field image. Weights in
+// framework (OIHW) order, FP32: W1 [16][4][3][3], b1 [16], W2 [16][16][3][3],
+// b2 [16], W3 [3][16][3][3], b3 [3].
+constexpr int kPostHidden = 16;
+constexpr int kPostW1 = 0;
+constexpr int kPostB1 = kPostW1 + kPostHidden * 4 * 9;
+constexpr int kPostW2 = kPostB1 + kPostHidden;
+constexpr int kPostB2 = kPostW2 + kPostHidden * kPostHidden * 9;
+constexpr int kPostW3 = kPostB2 + kPostHidden;
+constexpr int kPostB3 = kPostW3 + 3 * kPostHidden * 9;
+constexpr int kPostWeights = kPostB3 + 3;
+struct PostParams {
+    SphereK sphere;            // the hit mask of each pixel's ray
+    const float *w;            // [kPostWeights]
+    const float *in;           // [P][C] light-field image
+    float *out;                // [P][C] filtered image (must not overlap `in`)
+    uint32_t C;                // 3 or 4 (channel 3 is copied)
+};
+cudaError_t launch_post_filter(const PostParams &p, const ViewK &v, cudaStream_t st);
+
 // Fills the conservative-miss constants of a view for sphere (R, O) (lf_abi.cu).
 void fill_view_miss_consts(ViewK &k, double R, const double O[3]);
 

@@ -103,6 +103,8 @@ def lib():
                 "lf_precompute_table": (st, [C.POINTER(lf_precompute_desc), C.POINTER(lf_blob), vp, vp]),
                 "lf_render_volume": (st, [C.POINTER(lf_precompute_desc), C.POINTER(lf_blob),
                                           C.POINTER(lf_view), u32, vp, vp]),
+                "lf_post_filter": (st, [C.c_double, C.POINTER(C.c_double), u32, vp, C.POINTER(lf_view), u32,
+                                        vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -232,6 +234,18 @@ def lf_render_volume(desc: lf_precompute_desc, blobs, views, n_views: int, out_p
     ground truth of a light-field render of the precomputed table)."""
     _check(lib().lf_render_volume(C.byref(desc), blobs, views, n_views, C.c_void_p(out_ptr),
                                   C.c_void_p(stream or None)))
+
+
+LF_POST_WEIGHTS = 3347
+
+
+def lf_post_filter(radius: float, center, channels: int, weights_ptr: int, views, n_views: int, in_ptr: int,
+                   out_ptr: int, stream: int = 0):
+    """Learned post-filter of a light-field image (three 3x3 convolution layers,
+    residual on hit pixels)."""
+    c = (C.c_double * 3)(*[float(x) for x in center])
+    _check(lib().lf_post_filter(float(radius), c, channels, C.c_void_p(weights_ptr), views, n_views,
+                                C.c_void_p(in_ptr), C.c_void_p(out_ptr), C.c_void_p(stream or None)))
 
 
 def lf_device_sm_count() -> int:
