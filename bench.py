@@ -647,8 +647,9 @@ def run_post_filter(args):
             img, idx = lf.render(views, with_idx=True)
             if key == "light_field":
                 render_ms += timed(lambda: lf.render(views, out=img))
-                filtered = pf.apply(w, views, img)
-                filt_ms += timed(lambda: pf.apply(w, views, img, out=filtered))
+                filt = pf.PostFilter(w)
+                filtered = filt(views, img)
+                filt_ms += timed(lambda: filt(views, img, out=filtered))
                 out["filtered"] = filtered.cpu().numpy()
                 hit = idx[:, 0].cpu().numpy() >= 0
             out[key] = img.cpu().numpy()

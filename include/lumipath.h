@@ -291,16 +291,18 @@ lf_status lf_render_volume(const lf_precompute_desc *desc, const lf_blob *blobs_
  * hit = 1 if the pixel's ray meets the sphere (radius, center) by the FP32 test
  * of lf_render, else 0; the result is added to the input RGB of hit pixels,
  * other pixels are set to 0, and channel 3 (channels = 4) is copied.
- * weights_dev: LF_POST_WEIGHTS FP32 values (device), in this order and each in
+ * weights_host: LF_POST_WEIGHTS FP32 values (host, read during the call; they
+ * travel in the kernel's parameters), in this order and each in
  * [out][in][row][column] layout: W1 [16][4][3][3], b1 [16], W2 [16][16][3][3],
  * b2 [16], W3 [3][16][3][3], b3 [3]. in_dev / out_dev: [pixels][channels] FP32
  * (device; views laid out as for lf_render, channels 3 or 4; 4-byte aligned);
- * out_dev must not overlap in_dev. One launch per view; allocates nothing.
- * Errors: LF_ERR_INVALID_ARG (NULL, channels, radius, views as for lf_render,
- * overlapping buffers), LF_ERR_CUDA. Asynchronous on `stream`.
+ * out_dev must not overlap in_dev. One launch per 32 views; allocates nothing.
+ * Errors: LF_ERR_INVALID_ARG (NULL, channels, radius, non-finite weights,
+ * views as for lf_render, overlapping buffers), LF_ERR_CUDA. Asynchronous on
+ * `stream`.
  * ------------------------------------------------------------------------- */
 #define LF_POST_WEIGHTS 3347u
-lf_status lf_post_filter(double radius, const double center[3], uint32_t channels, const float *weights_dev,
+lf_status lf_post_filter(double radius, const double center[3], uint32_t channels, const float *weights_host,
                          const lf_view *views_host, uint32_t n_views, const float *in_dev, float *out_dev,
                          void *stream);
 

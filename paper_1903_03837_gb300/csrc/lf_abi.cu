@@ -638,20 +638,20 @@ lf_status lf_render_volume(const lf_precompute_desc *d, const lf_blob *blobs, co
     return LF_OK;
 }
 
-lf_status lf_post_filter(double radius, const double center[3], uint32_t channels, const float *weights_dev,
+lf_status lf_post_filter(double radius, const double center[3], uint32_t channels, const float *weights_host,
                          const lf_view *views, uint32_t n_views, const float *in_dev, float *out_dev,
                          void *stream)
 {
     NvtxRange nvtx_("lf_post_filter");
     g_err.clear();
     static_assert(lfk::kPostWeights == (int)LF_POST_WEIGHTS, "post-filter weight count");
-    if (!center || !weights_dev || !in_dev || !out_dev)
+    if (!center || !weights_host || !in_dev || !out_dev)
         return fail(LF_ERR_INVALID_ARG, "center, weights, in and out must not be NULL");
     if (!(radius > 0.0) || !std::isfinite(radius) || !finite3(center))
         return fail(LF_ERR_INVALID_ARG, "R must be positive and finite, O finite");
     if (channels != 3 && channels != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4");
-    if (misaligned(weights_dev, 4) || misaligned(in_dev, 4) || misaligned(out_dev, 4))
-        return fail(LF_ERR_INVALID_ARG, "weights, in and out must be 4-byte aligned");
+    if (misaligned(in_dev, 4) || misaligned(out_dev, 4))
+        return fail(LF_ERR_INVALID_ARG, "in and out must be 4-byte aligned");
     lf_status s = check_views(views, n_views);
     if (s != LF_OK) return s;
     uint64_t P = 0;
@@ -661,15 +661,32 @@ lf_status lf_post_filter(double radius, const double center[3], uint32_t channel
     }
     const uintptr_t a = (uintptr_t)in_dev, b = (uintptr_t)out_dev, bytes = (uintptr_t)(P * channels * 4);
     if (a < b + bytes && b < a + bytes) return fail(LF_ERR_INVALID_ARG, "out must not overlap in");
-    lfk::PostParams p{};
+    for (uint32_t k = 0; k < LF_POST_WEIGHTS; ++k)
+        if (!std::isfinite(weights_host[k])) return fail(LF_ERR_INVALID_ARG, "weight %u is not finite", k);
+    // PostParams holds 13 KB of weights: keep it off the stack
+    static thread_local lfk::PostParams p;
+    memset(&p, 0, sizeof p);
     lfk::fill_sphere_consts(p.sphere, radius, center);
-    p.w = weights_dev;
+    memcpy(p.w, weights_host, sizeof p.w);
     p.in = in_dev;
     p.out = out_dev;
     p.C = channels;
     cudaStream_t st = (cudaStream_t)stream;
-    for (uint32_t v = 0; v < n_views; ++v) {
-        cudaError_t e = lfk::launch_post_filter(p, camera_of(views[v]), st);
+    for (uint32_t v0 = 0; v0 < n_views; v0 += lfk::kPostMaxViews) {
+        const uint32_t nv = n_views - v0 < (uint32_t)lfk::kPostMaxViews ? n_views - v0 : (uint32_t)lfk::kPostMaxViews;
+        uint64_t tiles = 0;
+        for (uint32_t v = 0; v < nv; ++v) {
+            lfk::ViewK k = camera_of(views[v0 + v]);
+            k.tiles_x = (k.width + lfk::kPostTile - 1) / lfk::kPostTile;
+            k.tiles_y = (k.height + lfk::kPostTile - 1) / lfk::kPostTile;
+            p.views[v] = k;
+            p.tile_prefix[v] = (uint32_t)tiles;
+            tiles += (uint64_t)k.tiles_x * k.tiles_y;
+        }
+        if (tiles >= (1ull << 31)) return fail(LF_ERR_INVALID_ARG, "too many tiles in one launch");
+        p.tile_prefix[nv] = (uint32_t)tiles;
+        p.n_views = nv;
+        cudaError_t e = lfk::launch_post_filter(p, (unsigned)tiles, st);
         if (e != cudaSuccess) return cuda_fail(e, "post-filter");
     }
     return LF_OK;

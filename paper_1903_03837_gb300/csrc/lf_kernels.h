@@ -96,7 +96,8 @@ cudaError_t launch_volume_direct(const PrecomputeParams &p, const ViewK &v, cons
 
 // lf_post.cu: the learned post-filter of the light-field image. Weights in
 // framework (OIHW) order, FP32: W1 [16][4][3][3], b1 [16], W2 [16][16][3][3],
-// b2 [16], W3 [3][16][3][3], b3 [3].
+// b2 [16], W3 [3][16][3][3], b3 [3]; they travel in the kernel's parameter
+// block, so every multiply-add reads its weight as a constant-bank operand.
 constexpr int kPostHidden = 16;
 constexpr int kPostW1 = 0;
 constexpr int kPostB1 = kPostW1 + kPostHidden * 4 * 9;
@@ -105,14 +106,19 @@ constexpr int kPostB2 = kPostW2 + kPostHidden * kPostHidden * 9;
 constexpr int kPostW3 = kPostB2 + kPostHidden;
 constexpr int kPostB3 = kPostW3 + 3 * kPostHidden * 9;
 constexpr int kPostWeights = kPostB3 + 3;
+constexpr int kPostMaxViews = 32;       // views per launch
+constexpr int kPostTile = 14;           // output tile side (second layer: 16 x 16 = one CTA)
 struct PostParams {
-    SphereK sphere;            // the hit mask of each pixel's ray
-    const float *w;            // [kPostWeights]
-    const float *in;           // [P][C] light-field image
-    float *out;                // [P][C] filtered image (must not overlap `in`)
-    uint32_t C;                // 3 or 4 (channel 3 is copied)
+    SphereK sphere;                     // the hit mask of each pixel's ray
+    const float *in;                    // [P][C] light-field image
+    float *out;                         // [P][C] filtered image (must not overlap `in`)
+    uint32_t C;                         // 3 or 4 (channel 3 is copied)
+    uint32_t n_views;
+    uint32_t tile_prefix[kPostMaxViews + 1];
+    ViewK views[kPostMaxViews];         // tiles_x, tiles_y in kPostTile tiles
+    float w[kPostWeights];
 };
-cudaError_t launch_post_filter(const PostParams &p, const ViewK &v, cudaStream_t st);
+cudaError_t launch_post_filter(const PostParams &p, unsigned tiles, cudaStream_t st);
 
 // Fills the conservative-miss constants of a view for sphere (R, O) (lf_abi.cu).
 void fill_view_miss_consts(ViewK &k, double R, const double O[3]);

@@ -8,11 +8,16 @@
 // the render leaves them. Zero padding at the view border before every layer,
 // the same semantics as a framework convolution with padding 1.
 //
-// One CTA per 16x16 output tile of one view, FP32 on the CUDA cores: the
-// 22x22 input tile (with its mask), the 20x20 first-layer and the 18x18
-// second-layer activations and the 3,347 weights live in shared memory (66 KB),
-// so each layer reads the previous one from shared memory once per tap. The
-// layers are 16 channels wide: too narrow to fill a tensor-core tile.
+// One CTA of 256 threads per 14x14 output tile of one view (the tiles of all
+// views of a launch numbered consecutively), FP32 on the CUDA cores: the 20x20
+// input tile with its mask, the 18x18 first-layer and the 16x16 second-layer
+// activations live in shared memory (43.5 KB); the second layer, 86% of the
+// multiply-adds, is exactly one output position per thread. The weights are
+// part of the kernel's parameter block and every loop over them is unrolled,
+// so each multiply-add takes its weight as a constant-bank operand: one
+// instruction per multiply-add, and the activations are read from shared
+// memory once per tap for all 16 (or 3) output channels. The layers are 16
+// channels wide: too narrow to fill a tensor-core tile.
 #include <cuda_runtime.h>
 
 #include "lf_device.cuh"
@@ -20,27 +25,34 @@
 
 namespace lfk {
 
-constexpr int kPT = 16;                 // output tile side
-constexpr int kPIn = kPT + 6;           // input tile side (3 layers of radius 1)
-constexpr int kPH1 = kPT + 4;           // first-layer activations
-constexpr int kPH2 = kPT + 2;           // second-layer activations
-constexpr int kPostWeightsPad = (kPostWeights + 3) & ~3;
-constexpr size_t kPostSmem =
-    sizeof(float) * (kPostWeightsPad + 4 * kPIn * kPIn + kPostHidden * kPH1 * kPH1 + kPostHidden * kPH2 * kPH2);
+constexpr int kPT = kPostTile;          // 14: output tile side
+constexpr int kPH2 = kPT + 2;           // 16: second-layer activations
+constexpr int kPH1 = kPT + 4;           // 18: first-layer activations
+constexpr int kPIn = kPT + 6;           // 20: input tile (3 layers of radius 1)
 
-__global__ void __launch_bounds__(256) post_filter_kernel(const __grid_constant__ PostParams p,
-                                                          const __grid_constant__ ViewK v)
+__global__ void __launch_bounds__(256) post_filter_kernel(const __grid_constant__ PostParams p)
 {
-    extern __shared__ float sm[];
-    float *s_w = sm;
-    float *s_in = s_w + kPostWeightsPad;                 // [4][kPIn][kPIn]: R, G, B, hit mask
-    float *s_h1 = s_in + 4 * kPIn * kPIn;                // [16][kPH1][kPH1]
-    float *s_h2 = s_h1 + kPostHidden * kPH1 * kPH1;      // [16][kPH2][kPH2]
+    __shared__ float s_in[4 * kPIn * kPIn];              // R, G, B, hit mask
+    __shared__ float s_h1[kPostHidden * kPH1 * kPH1];
+    __shared__ float s_h2[kPostHidden * kPH2 * kPH2];
+    __shared__ uint32_t s_tile[3];
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kPT, y0 = blockIdx.y * kPT;
+    if (tid == 0) {
+        uint32_t lo = 0, hi = p.n_views;                 // largest v with tile_prefix[v] <= blockIdx.x
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (p.tile_prefix[mid] <= blockIdx.x) lo = mid; else hi = mid;
+        }
+        const uint32_t lt = blockIdx.x - p.tile_prefix[lo];
+        s_tile[0] = lo;
+        s_tile[1] = lt % p.views[lo].tiles_x;
+        s_tile[2] = lt / p.views[lo].tiles_x;
+    }
+    __syncthreads();
+    const ViewK &v = p.views[s_tile[0]];
+    const int x0 = (int)s_tile[1] * kPT, y0 = (int)s_tile[2] * kPT;
     const int W = (int)v.width, H = (int)v.height;
 
-    for (int k = tid; k < kPostWeights; k += blockDim.x) s_w[k] = __ldg(p.w + k);
     for (int k = tid; k < kPIn * kPIn; k += blockDim.x) {
         const int ty = k / kPIn, tx = k - ty * kPIn;
         const int x = x0 - 3 + tx, y = y0 - 3 + ty;
@@ -61,34 +73,38 @@ __global__ void __launch_bounds__(256) post_filter_kernel(const __grid_constant_
     }
     __syncthreads();
 
-    // layer 1: 4 -> 16 channels on the 20x20 ring-extended tile
+    // layer 1: 4 -> 16 channels on the 18x18 tile
     for (int k = tid; k < kPH1 * kPH1; k += blockDim.x) {
         const int ty = k / kPH1, tx = k - ty * kPH1;
         const int x = x0 - 2 + tx, y = y0 - 2 + ty;
         const bool inside = x >= 0 && y >= 0 && x < W && y < H;
-        float in[36];
+        float acc[kPostHidden];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int o = 0; o < kPostHidden; ++o) acc[o] = p.w[kPostB1 + o];
 #pragma unroll
-            for (int t = 0; t < 9; ++t) in[i * 9 + t] = s_in[i * kPIn * kPIn + (ty + t / 3) * kPIn + tx + t % 3];
-#pragma unroll 4
-        for (int o = 0; o < kPostHidden; ++o) {
-            float acc = s_w[kPostB1 + o];
+        for (int i = 0; i < 4; ++i) {
+            float in[9];
 #pragma unroll
-            for (int j = 0; j < 36; ++j) acc = fmaf(s_w[kPostW1 + o * 36 + j], in[j], acc);
-            s_h1[o * kPH1 * kPH1 + k] = inside ? fmaxf(acc, 0.0f) : 0.0f;
+            for (int t = 0; t < 9; ++t) in[t] = s_in[i * kPIn * kPIn + (ty + t / 3) * kPIn + tx + t % 3];
+#pragma unroll
+            for (int o = 0; o < kPostHidden; ++o)
+#pragma unroll
+                for (int t = 0; t < 9; ++t) acc[o] = fmaf(p.w[kPostW1 + (o * 4 + i) * 9 + t], in[t], acc[o]);
         }
+#pragma unroll
+        for (int o = 0; o < kPostHidden; ++o) s_h1[o * kPH1 * kPH1 + k] = inside ? fmaxf(acc[o], 0.0f) : 0.0f;
     }
     __syncthreads();
 
-    // layer 2: 16 -> 16 channels on the 18x18 tile
-    for (int k = tid; k < kPH2 * kPH2; k += blockDim.x) {
-        const int ty = k / kPH2, tx = k - ty * kPH2;
+    // layer 2: 16 -> 16 channels on the 16x16 tile, one position per thread
+    {
+        const int ty = tid / kPH2, tx = tid - ty * kPH2;
         const int x = x0 - 1 + tx, y = y0 - 1 + ty;
         const bool inside = x >= 0 && y >= 0 && x < W && y < H;
         float acc[kPostHidden];
 #pragma unroll
-        for (int o = 0; o < kPostHidden; ++o) acc[o] = s_w[kPostB2 + o];
+        for (int o = 0; o < kPostHidden; ++o) acc[o] = p.w[kPostB2 + o];
+#pragma unroll
         for (int i = 0; i < kPostHidden; ++i) {
             float in[9];
 #pragma unroll
@@ -96,45 +112,45 @@ __global__ void __launch_bounds__(256) post_filter_kernel(const __grid_constant_
 #pragma unroll
             for (int o = 0; o < kPostHidden; ++o)
 #pragma unroll
-                for (int t = 0; t < 9; ++t) acc[o] = fmaf(s_w[kPostW2 + (o * kPostHidden + i) * 9 + t], in[t], acc[o]);
+                for (int t = 0; t < 9; ++t)
+                    acc[o] = fmaf(p.w[kPostW2 + (o * kPostHidden + i) * 9 + t], in[t], acc[o]);
         }
 #pragma unroll
-        for (int o = 0; o < kPostHidden; ++o) s_h2[o * kPH2 * kPH2 + k] = inside ? fmaxf(acc[o], 0.0f) : 0.0f;
+        for (int o = 0; o < kPostHidden; ++o) s_h2[o * kPH2 * kPH2 + tid] = inside ? fmaxf(acc[o], 0.0f) : 0.0f;
     }
     __syncthreads();
 
     // layer 3: 16 -> 3 channels, added to the input colour of hit pixels
-    for (int k = tid; k < kPT * kPT; k += blockDim.x) {
-        const int ty = k / kPT, tx = k - ty * kPT;
+    if (tid < kPT * kPT) {
+        const int ty = tid / kPT, tx = tid - ty * kPT;
         const int x = x0 + tx, y = y0 + ty;
-        if (x >= W || y >= H) continue;
-        float acc[3] = {s_w[kPostB3], s_w[kPostB3 + 1], s_w[kPostB3 + 2]};
-        for (int i = 0; i < kPostHidden; ++i) {
-            float in[9];
+        if (x < W && y < H) {
+            float acc[3] = {p.w[kPostB3], p.w[kPostB3 + 1], p.w[kPostB3 + 2]};
 #pragma unroll
-            for (int t = 0; t < 9; ++t) in[t] = s_h2[i * kPH2 * kPH2 + (ty + t / 3) * kPH2 + tx + t % 3];
+            for (int i = 0; i < kPostHidden; ++i) {
+                float in[9];
 #pragma unroll
-            for (int o = 0; o < 3; ++o)
+                for (int t = 0; t < 9; ++t) in[t] = s_h2[i * kPH2 * kPH2 + (ty + t / 3) * kPH2 + tx + t % 3];
 #pragma unroll
-                for (int t = 0; t < 9; ++t) acc[o] = fmaf(s_w[kPostW3 + (o * kPostHidden + i) * 9 + t], in[t], acc[o]);
+                for (int o = 0; o < 3; ++o)
+#pragma unroll
+                    for (int t = 0; t < 9; ++t)
+                        acc[o] = fmaf(p.w[kPostW3 + (o * kPostHidden + i) * 9 + t], in[t], acc[o]);
+            }
+            const int c = (ty + 3) * kPIn + tx + 3;
+            const bool hit = s_in[3 * kPIn * kPIn + c] != 0.0f;
+            const uint64_t pix = v.out_offset + (uint64_t)y * W + x;
+            float *o = p.out + pix * p.C;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) o[ch] = hit ? s_in[ch * kPIn * kPIn + c] + acc[ch] : 0.0f;
+            if (p.C == 4) o[3] = __ldg(p.in + pix * 4 + 3);
         }
-        const int c = (ty + 3) * kPIn + tx + 3;
-        const bool hit = s_in[3 * kPIn * kPIn + c] != 0.0f;
-        const uint64_t pix = v.out_offset + (uint64_t)y * W + x;
-        float *o = p.out + pix * p.C;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) o[ch] = hit ? s_in[ch * kPIn * kPIn + c] + acc[ch] : 0.0f;
-        if (p.C == 4) o[3] = __ldg(p.in + pix * 4 + 3);
     }
 }
 
-cudaError_t launch_post_filter(const PostParams &p, const ViewK &v, cudaStream_t st)
+cudaError_t launch_post_filter(const PostParams &p, unsigned tiles, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(post_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kPostSmem);
-    if (e != cudaSuccess) return e;
-    const dim3 grid((v.width + kPT - 1) / kPT, (v.height + kPT - 1) / kPT);
-    post_filter_kernel<<<grid, 256, kPostSmem, st>>>(p, v);
+    post_filter_kernel<<<tiles, 256, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -239,12 +239,12 @@ def lf_render_volume(desc: lf_precompute_desc, blobs, views, n_views: int, out_p
 LF_POST_WEIGHTS = 3347
 
 
-def lf_post_filter(radius: float, center, channels: int, weights_ptr: int, views, n_views: int, in_ptr: int,
+def lf_post_filter(radius: float, center, channels: int, weights_host, views, n_views: int, in_ptr: int,
                    out_ptr: int, stream: int = 0):
     """Learned post-filter of a light-field image (three 3x3 convolution layers,
-    residual on hit pixels)."""
+    residual on hit pixels); weights_host: a ctypes array of LF_POST_WEIGHTS floats."""
     c = (C.c_double * 3)(*[float(x) for x in center])
-    _check(lib().lf_post_filter(float(radius), c, channels, C.c_void_p(weights_ptr), views, n_views,
+    _check(lib().lf_post_filter(float(radius), c, channels, weights_host, views, n_views,
                                 C.c_void_p(in_ptr), C.c_void_p(out_ptr), C.c_void_p(stream or None)))
 
 

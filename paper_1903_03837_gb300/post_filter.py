@@ -19,6 +19,7 @@ in another order); training is not on the render path.
 """
 from __future__ import annotations
 
+import ctypes
 import math
 from typing import List, Sequence, Tuple
 
@@ -151,18 +152,32 @@ def train(feats: torch.Tensor, targets: torch.Tensor, steps: int = 2000, batch: 
     return w.detach().contiguous(), history
 
 
+class PostFilter:
+    """Trained weights ready for the library's post-filter (a host copy: the
+    kernel takes them in its parameter block)."""
+
+    def __init__(self, w: torch.Tensor):
+        if w.numel() != N_WEIGHTS:
+            raise ValueError(f"weights must have {N_WEIGHTS} values")
+        flat = w.detach().to("cpu", torch.float32).reshape(-1).tolist()
+        self.host = (ctypes.c_float * N_WEIGHTS)(*flat)
+
+    def __call__(self, views: Sequence, image: torch.Tensor, R: float = 1.0, O=(0.0, 0.0, 0.0),
+                 out: torch.Tensor = None) -> torch.Tensor:
+        """The filter of a flat [P, C] light-field image of `views` (lf_post_filter)
+        into a new [P, C] image."""
+        api._need_cuda(image, "image")
+        if image.dtype != torch.float32 or image.dim() != 2:
+            raise ValueError("image must be a float32 [P, C] tensor")
+        if out is None:
+            out = torch.empty_like(image)
+        api._need_cuda(out, "out")
+        lp.lf_post_filter(R, O, int(image.shape[1]), self.host, lp.make_views(views), len(views),
+                          image.data_ptr(), out.data_ptr(), api._stream())
+        return out
+
+
 def apply(w: torch.Tensor, views: Sequence, image: torch.Tensor, R: float = 1.0, O=(0.0, 0.0, 0.0),
           out: torch.Tensor = None) -> torch.Tensor:
-    """The library's post-filter (lf_post_filter) of a flat [P, C] light-field
-    image of `views` into a new [P, C] image."""
-    api._need_cuda(w, "weights")
-    api._need_cuda(image, "image")
-    if w.dtype != torch.float32 or w.numel() != N_WEIGHTS:
-        raise ValueError(f"weights must be {N_WEIGHTS} float32 values")
-    P, C = int(image.shape[0]), int(image.shape[1])
-    if out is None:
-        out = torch.empty_like(image)
-    api._need_cuda(out, "out")
-    lp.lf_post_filter(R, O, C, w.data_ptr(), lp.make_views(views), len(views), image.data_ptr(), out.data_ptr(),
-                      api._stream())
-    return out
+    """One-off use of PostFilter(w)."""
+    return PostFilter(w)(views, image, R, O, out)

@@ -227,14 +227,18 @@ def test_post_filter_argument_errors_before_any_device_work():
     L = lp.lib()
     c3 = (C.c_double * 3)(0.0, 0.0, 0.0)
     v = _one_view()                    # 8 x 8 pixels
-    W, IN, OUT = C.c_void_p(0x10000), C.c_void_p(0x20000), C.c_void_p(0x30000)
+    W = (C.c_float * lp.LF_POST_WEIGHTS)()
+    IN, OUT = C.c_void_p(0x20000), C.c_void_p(0x30000)
     cases = [
         (1.0, None, 4, W, v, 1, IN, OUT), (1.0, c3, 4, None, v, 1, IN, OUT), (1.0, c3, 4, W, v, 1, None, OUT),
         (1.0, c3, 4, W, v, 1, IN, None), (0.0, c3, 4, W, v, 1, IN, OUT), (float("inf"), c3, 4, W, v, 1, IN, OUT),
         (1.0, c3, 5, W, v, 1, IN, OUT), (1.0, c3, 4, W, v, 0, IN, OUT), (1.0, c3, 4, W, None, 1, IN, OUT),
-        (1.0, c3, 4, C.c_void_p(0x10002), v, 1, IN, OUT),
+        (1.0, c3, 4, W, v, 1, C.c_void_p(0x20002), OUT),
         (1.0, c3, 4, W, v, 1, IN, C.c_void_p(0x20000 + 64 * 16 - 4)),      # out overlaps in's last pixel
     ]
     for args in cases:
         assert L.lf_post_filter(*args, None) == lp.LF_ERR_INVALID_ARG, (args, lp.lf_last_error())
     assert "overlap" in lp.lf_last_error()
+    W[7] = float("nan")
+    assert L.lf_post_filter(1.0, c3, 4, W, v, 1, IN, OUT, None) == lp.LF_ERR_INVALID_ARG
+    assert "finite" in lp.lf_last_error()
