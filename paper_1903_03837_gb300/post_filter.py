@@ -136,7 +136,7 @@ def train(feats: torch.Tensor, targets: torch.Tensor, steps: int = 2000, batch: 
           seed: int = 0) -> Tuple[torch.Tensor, List[float]]:
     """Adam on random batches of the training views; returns the weights and
     the loss every 100 steps."""
-    w = init_weights(seed).requires_grad_(True)
+    w = init_weights(seed, device=str(feats.device)).requires_grad_(True)
     opt = torch.optim.Adam([w], lr=lr)
     g = torch.Generator(device="cpu").manual_seed(seed + 1)
     history = []
