@@ -1,7 +1,8 @@
 """The image-quality measures of the benchmark (no GPU): the structural
 similarity index against its definition (Wang, Bovik, Sheikh, Simoncelli,
 IEEE TIP 2004) -- the measure the paper reports against its path-traced ground
-truth (Section 3) -- and the PSNR helper."""
+truth (Section 3) -- the PSNR helper, and the byte counts behind the roofline
+(algorithmic bytes per ray, compulsory 32-byte sectors of a frame)."""
 import math
 
 import numpy as np
@@ -78,3 +79,31 @@ def test_psnr_helper():
     test = ref + 0.1
     hit = np.array([True, False])
     assert abs(bench.psnr_db(ref, test, hit) - 10 * math.log10(1.0 / 0.01)) < 1e-9
+
+
+def test_algorithmic_bytes_per_ray():
+    # per hit ray: 25 texels + 5 row scales (quantised tables) + the 16-byte pixel; a miss: the pixel
+    assert bench.algorithmic_bytes(1, 1, "e4m3") == 25 * 4 + 5 * 4 + 16 == 136
+    assert bench.algorithmic_bytes(1, 1, "f16") == 25 * 8 + 5 * 4 + 16 == 236
+    assert bench.algorithmic_bytes(1, 1, "f32") == 25 * 16 + 16 == 416
+    assert bench.algorithmic_bytes(0, 10, "e4m3") == 160
+
+
+def test_compulsory_bytes_counts_distinct_sectors():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    N, rays = 37, 50
+    idx = rng.integers(0, 20, (12, 10)).astype(np.int32)
+    idx[3, 2] = -1                       # a missing origin neighbour
+    got = bench.compulsory_bytes(torch.from_numpy(idx), N, rays, "e4m3")
+    tex, sca = set(), set()
+    for r in idx:
+        for a in r[:5]:
+            if a < 0:
+                continue
+            sca.add((int(a) * 4) // 32)
+            for b in r[5:]:
+                if b >= 0:
+                    tex.add(((int(a) * N + int(b)) * 4) // 32)
+    assert got["texel_sectors"] == len(tex) and got["scale_sectors"] == len(sca)
+    assert got["bytes"] == rays * 16 + 32 * (len(tex) + len(sca))
