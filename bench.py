@@ -54,16 +54,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+RENDER_SOURCES = ("paper_1903_03837_gb300/csrc/lf_render.cu", "paper_1903_03837_gb300/csrc/lf_device.cuh",
+                  "paper_1903_03837_gb300/csrc/lf_kernels.h", "paper_1903_03837_gb300/csrc/lf_internal.h",
+                  "include/lumipath.h", "paper_1903_03837_gb300/build.py")
+
+
 def csrc_digest() -> str:
-    """SHA-256 over the CUDA sources of the library (name + content, sorted)."""
+    """SHA-256 over the files the render kernel is compiled from: its
+    translation unit and the headers it includes, and the build script that
+    holds the compiler flags (name + content, in this order)."""
     import hashlib
-    d = os.path.join(ROOT, "paper_1903_03837_gb300", "csrc")
     h = hashlib.sha256()
-    for n in sorted(os.listdir(d)):
-        if n.endswith((".cu", ".cuh", ".h")):
-            h.update(n.encode())
-            with open(os.path.join(d, n), "rb") as f:
-                h.update(f.read())
+    for n in RENDER_SOURCES:
+        h.update(n.encode())
+        with open(os.path.join(ROOT, n), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 
