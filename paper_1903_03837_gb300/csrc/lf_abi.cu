@@ -674,19 +674,9 @@ lf_status lf_post_filter(double radius, const double center[3], uint32_t channel
     cudaStream_t st = (cudaStream_t)stream;
     for (uint32_t v0 = 0; v0 < n_views; v0 += lfk::kPostMaxViews) {
         const uint32_t nv = n_views - v0 < (uint32_t)lfk::kPostMaxViews ? n_views - v0 : (uint32_t)lfk::kPostMaxViews;
-        uint64_t tiles = 0;
-        for (uint32_t v = 0; v < nv; ++v) {
-            lfk::ViewK k = camera_of(views[v0 + v]);
-            k.tiles_x = (k.width + lfk::kPostTile - 1) / lfk::kPostTile;
-            k.tiles_y = (k.height + lfk::kPostTile - 1) / lfk::kPostTile;
-            p.views[v] = k;
-            p.tile_prefix[v] = (uint32_t)tiles;
-            tiles += (uint64_t)k.tiles_x * k.tiles_y;
-        }
-        if (tiles >= (1ull << 31)) return fail(LF_ERR_INVALID_ARG, "too many tiles in one launch");
-        p.tile_prefix[nv] = (uint32_t)tiles;
+        for (uint32_t v = 0; v < nv; ++v) p.views[v] = camera_of(views[v0 + v]);
         p.n_views = nv;
-        cudaError_t e = lfk::launch_post_filter(p, (unsigned)tiles, st);
+        cudaError_t e = lfk::launch_post_filter(p, st);
         if (e != cudaSuccess) return cuda_fail(e, "post-filter");
     }
     return LF_OK;

@@ -107,18 +107,18 @@ constexpr int kPostW3 = kPostB2 + kPostHidden;
 constexpr int kPostB3 = kPostW3 + 3 * kPostHidden * 9;
 constexpr int kPostWeights = kPostB3 + 3;
 constexpr int kPostMaxViews = 32;       // views per launch
-constexpr int kPostTile = 14;           // output tile side (second layer: 16 x 16 = one CTA)
 struct PostParams {
     SphereK sphere;                     // the hit mask of each pixel's ray
     const float *in;                    // [P][C] light-field image
     float *out;                         // [P][C] filtered image (must not overlap `in`)
     uint32_t C;                         // 3 or 4 (channel 3 is copied)
     uint32_t n_views;
-    uint32_t tile_prefix[kPostMaxViews + 1];
-    ViewK views[kPostMaxViews];         // tiles_x, tiles_y in kPostTile tiles
+    uint32_t tile_prefix[kPostMaxViews + 1];   // filled by launch_post_filter
+    ViewK views[kPostMaxViews];         // cameras; tiles_x, tiles_y filled by launch_post_filter
     float w[kPostWeights];
 };
-cudaError_t launch_post_filter(const PostParams &p, unsigned tiles, cudaStream_t st);
+// Tiles the views (at most kPostMaxViews) and launches the filter.
+cudaError_t launch_post_filter(const PostParams &p, cudaStream_t st);
 
 // Fills the conservative-miss constants of a view for sphere (R, O) (lf_abi.cu).
 void fill_view_miss_consts(ViewK &k, double R, const double O[3]);
