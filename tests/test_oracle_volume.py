@@ -268,3 +268,23 @@ def test_light_field_render_converges_to_the_direct_render():
         assert hit.sum() == hits > 3000
         psnr.append(oracle.psnr(gt[:, :3], out[:, :3], hit))
     assert psnr[0] > 25 and psnr[1] > psnr[0] + 4 and psnr[2] > psnr[1] + 4, psnr
+
+
+def test_direct_pixel_along_a_chord_of_a_moved_sphere():
+    # the same correspondence for S of radius 2.5 centred away from the origin
+    v = lf_inputs.draw_volume(5, B=5, spp=1, steps=40, R=2.5, O=(0.5, -0.25, 1.0))
+    v.jitter = 0
+    M, N = 200, 90
+    O = np.asarray(v.O)
+    rng = np.random.default_rng(6)
+    pairs = [(int(rng.integers(M)), int(rng.integers(N))) for _ in range(40)]
+    views = []
+    for i, j in pairs:
+        p, q, d = chord(M, N, i, j)
+        a, b = O + v.R * p, O + v.R * q
+        views.append(lf_inputs.look_at(a - rng.uniform(0.5, 4.0) * d, b, 1, 1))
+    views = lf_inputs.pack_offsets(views)
+    out, hits = oracle.volume_pixels(v, views, lf_inputs.pixel_list(views))
+    want = oracle.volume_table(v, M, N, 4, texels=np.array(pairs))
+    assert hits == len(pairs)
+    np.testing.assert_allclose(out, want, rtol=0, atol=1e-5)
