@@ -27,7 +27,10 @@ marshals numpy arrays through ctypes. Functions:
   (Section 2, post-processing) in FP64
 * ``psnr``                                   -- image error against an FP64 render
 
-Parity unpinned: none. Each function is pinned in ``tests/test_oracle_pins.py``.
+Parity unpinned: none. Each function is pinned against facts that do not come
+from the oracle (closed forms, brute force, library routines, invariants) in
+``tests/test_oracle_pins.py`` (sampling path), ``tests/test_oracle_volume.py``
+(precompute and direct render) and ``tests/test_oracle_post.py`` (post-filter).
 """
 from __future__ import annotations
 
