@@ -306,8 +306,12 @@ lf_status lf_post_filter(double radius, const double center[3], uint32_t channel
                          const lf_view *views_host, uint32_t n_views, const float *in_dev, float *out_dev,
                          void *stream);
 
-/* Largest M + N that lf_render_noalloc accepts. */
+/* Largest M + N that lf_render_noalloc accepts, and the number of rays of one
+ * launch (one call's views, in chunks of 64) whose nearest-neighbour order the
+ * render kernel leaves to the exact pass it queues them for: past this many the
+ * exact pass renders every ray of that launch (the same image, more slowly). */
 #define LF_NOALLOC_MAX_POINTS 278528u
+#define LF_NOALLOC_MAX_DEFERRED 16384u
 
 /* Render without allocating any device memory. The paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc -- a process whose
@@ -319,21 +323,34 @@ lf_status lf_post_filter(double radius, const double center[3], uint32_t channel
  * {3,4}, or FP16/E4M3 codes [M][N][4] with row_scales_dev [M]; views, out_dev
  * and idx_dev as for lf_render; launch may be NULL for the default shape). It
  * writes the same image and indices as lf_create_table + lf_render.
- * The SF point caches and the status/queue words live in one fixed device
- * array inside the library (32 B per point for up to LF_NOALLOC_MAX_POINTS
- * points, about 8.5 MiB), which every GPU that loads the library keeps until
- * the process exits. Each call rebuilds that content on `stream` and leaves
- * the last call's contents behind; calls that overlap on the GPU (other
- * streams or threads) race on it. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, once per device, with that
- * device current); make that first call before any stream capture.
+ * The SF point caches, the status/queue words and the queue of rays left to
+ * the exact pass live in one fixed device array inside the library (32 B per
+ * point for up to LF_NOALLOC_MAX_POINTS points plus 8 B per queued ray for up
+ * to LF_NOALLOC_MAX_DEFERRED rays, about 8.6 MiB), which every GPU that loads
+ * the library keeps until the process exits. Each call rebuilds that content
+ * on `stream` and leaves the last call's contents behind; calls that overlap
+ * on the GPU (other streams or threads) race on it. Every call looks up the
+ * array's device address (cudaGetSymbolAddress, with the caller's device
+ * current; it allocates nothing, and the address is valid only for the
+ * context that looked it up); the first call on a device may load the
+ * library's device code, so make it before any stream capture.
  * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Device-side checks (an index out of range) are recorded in the array's
+ * status word; lf_noalloc_sync_status reads them.
  * Errors: LF_ERR_INVALID_ARG (including M + N > LF_NOALLOC_MAX_POINTS, with a
  * message saying so), LF_ERR_UNSUPPORTED, LF_ERR_CUDA. */
 lf_status lf_render_noalloc(const lf_table_desc *desc, const void *radiance_dev,
                             const float *row_scales_dev, const lf_view *views_host,
                             uint32_t n_views, const lf_launch *launch, float *out_dev,
                             int32_t *idx_dev, void *stream);
+
+/* Synchronise `stream` and report the status word of lf_render_noalloc's
+ * device array on the current device, as lf_sync_status does for a table:
+ * LF_OK, or LF_ERR_DEVICE_CHECK if a kernel of the last lf_render_noalloc call
+ * on this device recorded a failed check (the word is then cleared; every
+ * lf_render_noalloc call clears it when it starts). Allocates nothing; no
+ * counterpart in the paper. Errors: LF_ERR_CUDA, LF_ERR_DEVICE_CHECK. */
+lf_status lf_noalloc_sync_status(void *stream);
 
 /* Number of SMs of the current device (0 without one) and the library
  * version string. */

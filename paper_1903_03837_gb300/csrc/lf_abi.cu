@@ -114,6 +114,11 @@ lf_status volume_params(const lf_precompute_desc *d, const lf_blob *blobs, float
     return LF_OK;
 }
 
+
+}  // namespace
+
+namespace lfk {
+
 lf_status check_launch(const lf_launch *c)
 {
     if (!c) return fail(LF_ERR_INVALID_ARG, "launch config is NULL");
@@ -126,8 +131,8 @@ lf_status check_launch(const lf_launch *c)
     if (c->tile_w % ww || c->tile_h % wh)
         return fail(LF_ERR_INVALID_ARG, "tile %ux%u is not a whole number of %ux%u warp tiles",
                     c->tile_w, c->tile_h, ww, wh);
-    if (c->tile_w * c->tile_h > (uint32_t)lfk::kMaxBlock)
-        return fail(LF_ERR_INVALID_ARG, "tile %ux%u exceeds %d threads", c->tile_w, c->tile_h, lfk::kMaxBlock);
+    if (c->tile_w * c->tile_h > (uint32_t)kMaxBlock)
+        return fail(LF_ERR_INVALID_ARG, "tile %ux%u exceeds %d threads", c->tile_w, c->tile_h, kMaxBlock);
     if (c->order > 1 || c->persistent > 1)
         return fail(LF_ERR_INVALID_ARG, "order must be 0/1 and persistent 0/1");
     if (c->ctas_per_sm > 64) return fail(LF_ERR_INVALID_ARG, "ctas_per_sm > 64");
@@ -153,9 +158,9 @@ lf_status check_views(const lf_view *views, uint32_t n)
 }
 
 // The camera of a view (no tiling, no miss constants).
-lfk::ViewK camera_of(const lf_view &w)
+ViewK camera_of(const lf_view &w)
 {
-    lfk::ViewK k;
+    ViewK k;
     memset(&k, 0, sizeof k);
     for (int i = 0; i < 3; ++i) {
         k.eye[i] = w.eye[i];
@@ -171,14 +176,43 @@ lfk::ViewK camera_of(const lf_view &w)
     return k;
 }
 
-lfk::ViewK to_viewk(const lf_view &w, const lf_launch &L, const lf_table *t)
+ViewK view_params(const lf_view &w, const lf_launch &L, double R, const double O[3])
 {
-    lfk::ViewK k = camera_of(w);
+    ViewK k = camera_of(w);
     k.tiles_x = (w.width + L.tile_w - 1) / L.tile_w;
     k.tiles_y = (w.height + L.tile_h - 1) / L.tile_h;
-    lfk::fill_view_miss_consts(k, t->desc.radius, t->desc.center);
+    fill_view_miss_consts(k, R, O);
     return k;
 }
+
+// Checks of a table description shared by lf_create_table and
+// lf_render_noalloc: radius and centre, point counts, channels, storage type,
+// neighbour count and flags.
+lf_status check_desc(const lf_table_desc *d)
+{
+    if (!d) return fail(LF_ERR_INVALID_ARG, "desc is NULL");
+    if (!(std::isfinite(d->radius) && d->radius > 0.0))
+        return fail(LF_ERR_INVALID_ARG, "radius must be finite and > 0");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(d->center[k])) return fail(LF_ERR_INVALID_ARG, "center must be finite");
+    const uint32_t M = d->n_origins, N = d->n_directions, C = d->channels;
+    if (M == 0 || N == 0 || M > (1u << 24) || N > (1u << 24))
+        return fail(LF_ERR_INVALID_ARG, "point counts must be in [1, 2^24] (M=%u, N=%u)", M, N);
+    if (C != 3 && C != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4 (got %u)", C);
+    if (d->dtype != LF_DTYPE_F32 && d->dtype != LF_DTYPE_F16 && d->dtype != LF_DTYPE_E4M3)
+        return fail(LF_ERR_INVALID_ARG, "unknown dtype %d", d->dtype);
+    if (d->k_nearest != 0 && d->k_nearest != 1 && d->k_nearest != 5 && d->k_nearest != 9)
+        return fail(LF_ERR_UNSUPPORTED, "k_nearest=%u: 1, 5 or 9 neighbours per hit are built", d->k_nearest);
+    if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
+        return fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
+    if ((d->flags & LF_TABLE_UPPER_HEMISPHERE) && M < 2)
+        return fail(LF_ERR_INVALID_ARG, "an upper-hemisphere table needs M >= 2");
+    return LF_OK;
+}
+
+}  // namespace lfk
+
+namespace {
 
 template <int MAXV>
 lf_status run_chunk(const lf_table *t, const lfk::RenderParamsBase &base, const lf_view *views,
@@ -190,7 +224,7 @@ lf_status run_chunk(const lf_table *t, const lfk::RenderParamsBase &base, const 
     const lf_launch &L = t->launch;
     uint64_t tiles = 0;
     for (uint32_t v = 0; v < nv; ++v) {
-        p.views[v] = to_viewk(views[v], L, t);
+        p.views[v] = lfk::view_params(views[v], L, t->desc.radius, t->desc.center);
         p.tile_prefix[v] = (uint32_t)tiles;
         tiles += (uint64_t)p.views[v].tiles_x * p.views[v].tiles_y;
     }
@@ -198,6 +232,8 @@ lf_status run_chunk(const lf_table *t, const lfk::RenderParamsBase &base, const 
     p.tile_prefix[nv] = (uint32_t)tiles;
     p.n_views = nv;
     p.total_tiles = (uint32_t)tiles;
+    p.total_pixels = 0;
+    for (uint32_t v = 0; v < nv; ++v) p.total_pixels += (uint64_t)views[v].width * views[v].height;
     unsigned block = L.tile_w * L.tile_h;
     unsigned grid = (unsigned)tiles;
     if (L.persistent) {
@@ -221,7 +257,7 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
               const float *grad_out, float *grad, void *stream, const int32_t *idx_in = nullptr,
               bool out_f16 = false)
 {
-    lf_status s = check_views(views, n_views);
+    lf_status s = lfk::check_views(views, n_views);
     if (s != LF_OK) return s;
     const uintptr_t va = t->C == 4 ? 16 : 4;      // float4 image / gradient accesses for 4 channels
     const uintptr_t oa = out_f16 ? (t->C == 4 ? 8 : 2) : va;
@@ -250,6 +286,10 @@ lf_status run(const lf_table *t, const lf_view *views, uint32_t n_views, float *
     b.status = t->scratch;
     b.queue = t->scratch + 1;
     b.done = t->scratch + 2;
+    b.defer_done = t->scratch + 3;
+    b.defer_count = reinterpret_cast<unsigned long long *>(t->scratch + 4);
+    b.defer_items = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(t->scratch) + lfk::kWordsBytes);
+    b.defer_cap = lfk::kDeferCap;
     b.tile_w = t->launch.tile_w;
     b.tile_h = t->launch.tile_h;
     b.warp_w = t->launch.warp_w;
@@ -344,24 +384,11 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
     g_err.clear();
     if (!out) return fail(LF_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (!d) return fail(LF_ERR_INVALID_ARG, "desc is NULL");
+    lf_status ds = lfk::check_desc(d);
+    if (ds != LF_OK) return ds;
     if (!radiance_dev) return fail(LF_ERR_INVALID_ARG, "radiance is NULL");
-    if (!(std::isfinite(d->radius) && d->radius > 0.0))
-        return fail(LF_ERR_INVALID_ARG, "radius must be finite and > 0");
-    for (int k = 0; k < 3; ++k)
-        if (!std::isfinite(d->center[k])) return fail(LF_ERR_INVALID_ARG, "center must be finite");
     const uint32_t M = d->n_origins, N = d->n_directions, C = d->channels;
-    if (M == 0 || N == 0 || M > (1u << 24) || N > (1u << 24))
-        return fail(LF_ERR_INVALID_ARG, "point counts must be in [1, 2^24] (M=%u, N=%u)", M, N);
-    if (C != 3 && C != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4 (got %u)", C);
-    if (d->dtype != LF_DTYPE_F32 && d->dtype != LF_DTYPE_F16 && d->dtype != LF_DTYPE_E4M3)
-        return fail(LF_ERR_INVALID_ARG, "unknown dtype %d", d->dtype);
-    if (d->k_nearest != 0 && d->k_nearest != 1 && d->k_nearest != 5 && d->k_nearest != 9)
-        return fail(LF_ERR_UNSUPPORTED, "k_nearest=%u: 1, 5 or 9 neighbours per hit are built", d->k_nearest);
-    if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
-        return fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
     const bool upper = (d->flags & LF_TABLE_UPPER_HEMISPHERE) != 0;
-    if (upper && M < 2) return fail(LF_ERR_INVALID_ARG, "an upper-hemisphere table needs M >= 2");
     const uint32_t rows = upper ? M / 2 : M;
     const bool quant = d->dtype != LF_DTYPE_F32;
     if (quant && !row_scales_dev) return fail(LF_ERR_INVALID_ARG, "F16/E4M3 tables need row scales");
@@ -393,9 +420,9 @@ lf_status lf_create_table(const lf_table_desc *d, const void *radiance_dev, cons
 
     e = cudaMalloc(&t->points, sizeof(float4) * 2ull * ((uint64_t)M + N));
     if (e != cudaSuccess) return bail(cuda_fail(e, "point cache allocation"));
-    e = cudaMalloc(&t->scratch, 4 * sizeof(uint32_t));
+    e = cudaMalloc(&t->scratch, lfk::kWordsBytes + sizeof(unsigned long long) * (size_t)lfk::kDeferCap);
     if (e != cudaSuccess) return bail(cuda_fail(e, "scratch allocation"));
-    e = cudaMemsetAsync(t->scratch, 0, 4 * sizeof(uint32_t), st);
+    e = cudaMemsetAsync(t->scratch, 0, lfk::kWordsBytes, st);
     if (e != cudaSuccess) return bail(cuda_fail(e, "scratch clear"));
     e = lfk::launch_build_points(M, t->points, t->points + M, st);
     if (e == cudaSuccess) e = lfk::launch_build_points(N, t->points + 2 * (uint64_t)M, t->points + 2 * (uint64_t)M + N, st);
@@ -451,7 +478,7 @@ void lf_destroy(lf_table *t)
 lf_status lf_set_launch(lf_table *t, const lf_launch *cfg)
 {
     if (!t) return fail(LF_ERR_INVALID_ARG, "table is NULL");
-    lf_status s = check_launch(cfg);
+    lf_status s = lfk::check_launch(cfg);
     if (s != LF_OK) return s;
     t->launch = *cfg;
     return LF_OK;
@@ -626,13 +653,13 @@ lf_status lf_render_volume(const lf_precompute_desc *d, const lf_blob *blobs, co
     static thread_local lfk::PrecomputeParams P;
     lf_status s = volume_params(d, blobs, out_dev, P);
     if (s != LF_OK) return s;
-    s = check_views(views, n_views);
+    s = lfk::check_views(views, n_views);
     if (s != LF_OK) return s;
     lfk::SphereK S{};
     lfk::fill_sphere_consts(S, d->radius, d->center);
     cudaStream_t st = (cudaStream_t)stream;
     for (uint32_t v = 0; v < n_views; ++v) {
-        cudaError_t e = lfk::launch_volume_direct(P, camera_of(views[v]), S, d->radius, st);
+        cudaError_t e = lfk::launch_volume_direct(P, lfk::camera_of(views[v]), S, d->radius, st);
         if (e != cudaSuccess) return cuda_fail(e, "direct volume render");
     }
     return LF_OK;
@@ -652,7 +679,7 @@ lf_status lf_post_filter(double radius, const double center[3], uint32_t channel
     if (channels != 3 && channels != 4) return fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4");
     if (misaligned(in_dev, 4) || misaligned(out_dev, 4))
         return fail(LF_ERR_INVALID_ARG, "in and out must be 4-byte aligned");
-    lf_status s = check_views(views, n_views);
+    lf_status s = lfk::check_views(views, n_views);
     if (s != LF_OK) return s;
     uint64_t P = 0;
     for (uint32_t v = 0; v < n_views; ++v) {
@@ -674,7 +701,7 @@ lf_status lf_post_filter(double radius, const double center[3], uint32_t channel
     cudaStream_t st = (cudaStream_t)stream;
     for (uint32_t v0 = 0; v0 < n_views; v0 += lfk::kPostMaxViews) {
         const uint32_t nv = n_views - v0 < (uint32_t)lfk::kPostMaxViews ? n_views - v0 : (uint32_t)lfk::kPostMaxViews;
-        for (uint32_t v = 0; v < nv; ++v) p.views[v] = camera_of(views[v0 + v]);
+        for (uint32_t v = 0; v < nv; ++v) p.views[v] = lfk::camera_of(views[v0 + v]);
         p.n_views = nv;
         cudaError_t e = lfk::launch_post_filter(p, st);
         if (e != cudaSuccess) return cuda_fail(e, "post-filter");

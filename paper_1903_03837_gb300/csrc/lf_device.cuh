@@ -73,20 +73,35 @@ __device__ __forceinline__ float azimuth_turns(float y, float x)
 // ---------------------------------------------------------------------------
 // Camera ray and sphere intersection: IEEE FP32, fixed order, no contraction.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float3 camera_dir(const ViewK &v, uint32_t x, uint32_t y)
+// The camera ray's direction before normalisation is the column term
+// fwd + nx*right of pixel column x plus the row term ny*up of pixel row y (in
+// this operation order), so a tile can compute its columns and rows once.
+__device__ __forceinline__ float3 camera_col(const ViewK &v, uint32_t x)
 {
     float px = __fadd_rn(__uint2float_rn(x), 0.5f);
-    float py = __fadd_rn(__uint2float_rn(y), 0.5f);
     float sx = __fdiv_rn(__fadd_rn(px, px), __uint2float_rn(v.width));
-    float sy = __fdiv_rn(__fadd_rn(py, py), __uint2float_rn(v.height));
     float nx = __fmul_rn(__fsub_rn(sx, 1.0f), v.tan_x);
+    return make_float3(__fadd_rn(v.fwd[0], __fmul_rn(nx, v.right[0])), __fadd_rn(v.fwd[1], __fmul_rn(nx, v.right[1])),
+                       __fadd_rn(v.fwd[2], __fmul_rn(nx, v.right[2])));
+}
+__device__ __forceinline__ float3 camera_row(const ViewK &v, uint32_t y)
+{
+    float py = __fadd_rn(__uint2float_rn(y), 0.5f);
+    float sy = __fdiv_rn(__fadd_rn(py, py), __uint2float_rn(v.height));
     float ny = __fmul_rn(__fsub_rn(1.0f, sy), v.tan_y);
-    float vx = __fadd_rn(__fadd_rn(v.fwd[0], __fmul_rn(nx, v.right[0])), __fmul_rn(ny, v.up[0]));
-    float vy = __fadd_rn(__fadd_rn(v.fwd[1], __fmul_rn(nx, v.right[1])), __fmul_rn(ny, v.up[1]));
-    float vz = __fadd_rn(__fadd_rn(v.fwd[2], __fmul_rn(nx, v.right[2])), __fmul_rn(ny, v.up[2]));
+    return make_float3(__fmul_rn(ny, v.up[0]), __fmul_rn(ny, v.up[1]), __fmul_rn(ny, v.up[2]));
+}
+// Unit ray direction from a column term and a row term.
+__device__ __forceinline__ float3 camera_dir_cr(float3 c, float3 r)
+{
+    float vx = __fadd_rn(c.x, r.x), vy = __fadd_rn(c.y, r.y), vz = __fadd_rn(c.z, r.z);
     float l2 = __fadd_rn(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)), __fmul_rn(vz, vz));
     float l = __fsqrt_rn(l2);
     return make_float3(__fdiv_rn(vx, l), __fdiv_rn(vy, l), __fdiv_rn(vz, l));
+}
+__device__ __forceinline__ float3 camera_dir(const ViewK &v, uint32_t x, uint32_t y)
+{
+    return camera_dir_cr(camera_col(v, x), camera_row(v, y));
 }
 
 // Front hit h_o and back hit h_d; false if the discriminant is <= 0 (tangential
@@ -268,22 +283,26 @@ __device__ __forceinline__ double dist2_fp64(const PointSetK &P, int32_t i, cons
 // Inverse SF mapping, extended to the 5 nearest points (Section 2).
 //
 // Candidate sources:
-//   FULL   n <= 128: every point (slot = index).
+//   FULL   n <= 128: every point.
 //   POLE   the continuous index (n(1-z)-1)/2 of the hit lies within 16 of a
-//          pole: the 64 points nearest that pole (slot = offset).
+//          pole: the 64 points nearest that pole.
 //   WINDOW otherwise: 12 lattice corners around round(u, v) (below), where
 //          (u, v) are the hit's coordinates in the local Fibonacci basis of zone k.
+// Every source numbers its candidates by a slot s, and candidate s has index
+// b0 + (s & 3) G0 + (s >> 2) G1 (a scan takes G0 = 1, G1 = 4: index b0 + s).
+//
 // Tier 1 ranks every candidate by an FP32 squared distance from the hi parts
 // only (key = float bits with the low bits replaced by the slot) and keeps the
-// 7 smallest keys. With the rigorous error bound e1 of that distance, the
-// tier-1 order of the top 5 is the exact one when each of the top 6 keys'
-// upper bound lies below the next key's lower bound (by more than an FP64
-// rounding): the common case, which needs double-float distances of those 5
-// only (for the weights). Otherwise the true 5 nearest still lie among the
-// tier-1 top 6 when the 5th key's upper bound is below the 7th key's lower
-// bound; tier 2 recomputes those 6 in double-float, sorts them and accepts the
-// order when every consecutive gap exceeds the tier-2 error. Anything
-// uncertain is ranked again in FP64 by (distance, index).
+// 7 smallest keys, sorted. With the rigorous error bound e1 of that distance,
+// the tier-1 order of the top 5 is the exact one when each of the top 6 keys'
+// upper bound lies below the next key's lower bound by more than any FP64
+// rounding (the order certificate): the common case, which needs double-float
+// distances of those 5 only (for the weights). Otherwise (out of line) the
+// true 5 nearest still lie among the tier-1 top 6 when the 5th key's upper
+// bound is below the 7th key's lower bound; tier 2 recomputes those 6 in
+// double-float, sorts them and accepts the order when every consecutive gap
+// exceeds the tier-2 error. Anything uncertain is ranked again in FP64 by
+// (distance, index) over all candidates.
 // ---------------------------------------------------------------------------
 #define LF_CS(a, b)                          \
     {                                        \
@@ -292,19 +311,18 @@ __device__ __forceinline__ double dist2_fp64(const PointSetK &P, int32_t i, cons
         k[a] = lo_;                          \
     }
 
-// Batcher odd-even merge sort of 16 keys, pruned to the comparators that
-// reach outputs 0..6 (the 7 smallest, sorted; 54 comparators).
-__device__ __forceinline__ void select7_of16(uint32_t k[16])
+// The 7 smallest of 12 keys, sorted into k[0..6]: Batcher's odd-even merge
+// sort of 16 inputs with inputs 12..15 fixed at +inf, pruned to the
+// comparators that reach outputs 0..6 (37 comparators; the compiler drops the
+// max of the 7 whose larger output is never read).
+__device__ __forceinline__ void select7_of12(uint32_t k[12])
 {
     LF_CS(0, 1) LF_CS(2, 3) LF_CS(0, 2) LF_CS(1, 3) LF_CS(1, 2) LF_CS(4, 5) LF_CS(6, 7)
     LF_CS(4, 6) LF_CS(5, 7) LF_CS(5, 6) LF_CS(0, 4) LF_CS(2, 6) LF_CS(2, 4) LF_CS(1, 5)
     LF_CS(3, 7) LF_CS(3, 5) LF_CS(1, 2) LF_CS(3, 4) LF_CS(5, 6) LF_CS(8, 9) LF_CS(10, 11)
-    LF_CS(8, 10) LF_CS(9, 11) LF_CS(9, 10) LF_CS(12, 13) LF_CS(14, 15) LF_CS(12, 14)
-    LF_CS(13, 15) LF_CS(13, 14) LF_CS(8, 12) LF_CS(10, 14) LF_CS(10, 12) LF_CS(9, 13)
-    LF_CS(11, 15) LF_CS(11, 13) LF_CS(9, 10) LF_CS(11, 12) LF_CS(13, 14) LF_CS(0, 8)
-    LF_CS(4, 12) LF_CS(4, 8) LF_CS(2, 10) LF_CS(6, 14) LF_CS(6, 10) LF_CS(2, 4) LF_CS(6, 8)
-    LF_CS(1, 9) LF_CS(5, 13) LF_CS(5, 9) LF_CS(3, 11) LF_CS(3, 5) LF_CS(1, 2) LF_CS(3, 4)
-    LF_CS(5, 6)
+    LF_CS(8, 10) LF_CS(9, 11) LF_CS(9, 10) LF_CS(0, 8) LF_CS(4, 8) LF_CS(2, 10) LF_CS(6, 10)
+    LF_CS(2, 4) LF_CS(6, 8) LF_CS(1, 9) LF_CS(5, 9) LF_CS(3, 11) LF_CS(3, 5) LF_CS(1, 2)
+    LF_CS(3, 4) LF_CS(5, 6)
 }
 
 // Optimal 12-comparator network sorting 6 keys.
@@ -324,19 +342,36 @@ __device__ __forceinline__ void insert7(uint32_t s[7], uint32_t key)
     }
 }
 
-// Lattice window: (u, v) rounded to the nearest cell corner (ru, rv); the
-// candidates are the 3x3 corners around it plus three corners on the side of
-// the sign quadrant of (u - ru, v - rv). A brute-force study over n = 256 ...
-// 262,144 (3.3 M queries, (u, v) perturbed by +-2e-3, zone number flipped by
-// +-1) found the true 5 nearest always inside these 12 corners away from the
-// poles.
-struct Window {
-    int32_t base, F0, F1;
-    int32_t ext[3];          // index offsets of the three quadrant corners
-    bool interior;           // every candidate index lies in [0, n)
+// Candidate source of one query: slot s -> index b0 + (s & 3) G0 + (s >> 2) G1.
+struct Source {
+    int32_t b0, G0, G1;
+    int32_t scan_cnt;        // 0: lattice window, else the number of scanned points
+    int bits;                // tier-1 slot bits
+    bool interior;           // every window candidate lies in [0, n)
 };
 
-__device__ __forceinline__ Window lattice_window(const PointSetK &P, float3 qh)
+__device__ __forceinline__ int32_t source_index(const Source &s, uint32_t slot)
+{
+    return s.b0 + (int32_t)(slot & 3u) * s.G0 + (int32_t)(slot >> 2) * s.G1;
+}
+
+// Lattice window. (u, v) rounded to the nearest cell corner (ru, rv) = c; the
+// candidates are the 3x3 corners around c plus three corners on the side of
+// the sign quadrant of (u - ru, v - rv): with (du, dv) the offsets from c,
+//   (+,+): (1,2) (2,-1) (2,0)      (-,-): (-2,0) (-1,-2) (-2,1)
+//   (+,-): (-1,-2) (0,-2) (2,-1)   (-,+): (-2,1) (0,2) (1,2).
+// The four quadrant sets are one set turned by quarter turns of the lattice
+// (du, dv) -> (-dv, du), under which the 3x3 block is invariant, so the
+// window is the fixed offsets {-1,0,1}^2 + {(1,2), (2,-1), (2,0)} in the basis
+// (G0, G1) = (F0, F1), (-F0, -F1), (-F1, F0) or (F1, -F0) of the quadrant
+// (+,+), (-,-), (+,-), (-,+). In slots s = (du + 1) + 4 (dv + 1) these are
+// s = 0..10 and 14, and candidate s has index c - G0 - G1 + (s & 3) G0 +
+// (s >> 2) G1. The window is complete for the 5 nearest (tests/
+// test_window_study.py: brute force against this window for n = 256 ... 2^24
+// with the lattice coordinates and the zone perturbed by more than their FP32
+// error). Outside the pole scan the zone is k >= 6 (F_k >= 8), so the 12
+// corners have distinct indices.
+__device__ __forceinline__ Source lattice_window(const PointSetK &P, float3 qh)
 {
     float z = qh.z;
     float omz2 = __fmul_rn(__fsub_rn(1.0f, z), __fadd_rn(1.0f, z));
@@ -351,74 +386,45 @@ __device__ __forceinline__ Window lattice_window(const PointSetK &P, float3 qh)
     float v = sg * __fmaf_rn((float)F0, t, -e0 * ic);
     float ru = rintf(u), rv = rintf(v);
     bool pu = u >= ru, pv = v >= rv;
-    Window w;
-    w.base = (int32_t)ru * F0 + (int32_t)rv * F1;
-    w.F0 = F0;
-    w.F1 = F1;
-    // quadrant corners (du, dv): (-,-): (-2,0) (-1,-2) (-2,1); (-,+): (-2,1) (0,2) (1,2);
-    //                            (+,-): (-1,-2) (0,-2) (2,-1); (+,+): (1,2) (2,-1) (2,0)
-    if (!pu && !pv) {
-        w.ext[0] = -2 * F0; w.ext[1] = -F0 - 2 * F1; w.ext[2] = -2 * F0 + F1;
-    } else if (!pu) {
-        w.ext[0] = -2 * F0 + F1; w.ext[1] = 2 * F1; w.ext[2] = F0 + 2 * F1;
-    } else if (!pv) {
-        w.ext[0] = -F0 - 2 * F1; w.ext[1] = -2 * F1; w.ext[2] = 2 * F0 - F1;
-    } else {
-        w.ext[0] = F0 + 2 * F1; w.ext[1] = 2 * F0 - F1; w.ext[2] = 2 * F0;
-    }
+    Source s;
+    const int32_t base = (int32_t)ru * F0 + (int32_t)rv * F1;
+    s.G0 = pu ? (pv ? F0 : -F1) : (pv ? F1 : -F0);
+    s.G1 = pu ? (pv ? F1 : F0) : (pv ? -F0 : -F1);
+    s.b0 = base - s.G0 - s.G1;
     const int32_t reach = 2 * (F0 + F1);
-    w.interior = (w.base - reach >= 0) && (w.base + reach < (int32_t)P.n);
-    return w;
+    s.interior = (base - reach >= 0) && (base + reach < (int32_t)P.n);
+    s.scan_cnt = 0;
+    s.bits = 4;
+    return s;
 }
 
 constexpr int kWindow = 12;
 
-__device__ __forceinline__ int32_t window_index(const Window &w, int slot)
-{
-    if (slot < 9) return w.base + (slot / 3 - 1) * w.F0 + (slot % 3 - 1) * w.F1;
-    return w.base + w.ext[slot - 9];
-}
+// Slot of window candidate j (0..11).
+__device__ __forceinline__ constexpr uint32_t slot5(int j) { return j < 11 ? (uint32_t)j : 14u; }
 
 // Candidate source of one query (see above).
-struct Source {
-    Window w;
-    int32_t scan_base, scan_cnt;   // scan_cnt == 0: window
-    int bits;                      // tier-1 slot bits
-};
-
 __device__ __forceinline__ Source candidate_source(const PointSetK &P, float3 qh)
 {
     const int32_t n = (int32_t)P.n;
     Source s;
-    s.w.base = s.w.F0 = s.w.F1 = 0;
-    s.w.ext[0] = s.w.ext[1] = s.w.ext[2] = 0;
-    s.w.interior = false;
-    s.scan_base = 0;
-    s.scan_cnt = 0;
-    s.bits = 4;
+    s.b0 = 0;
+    s.G0 = 1;
+    s.G1 = 4;
+    s.interior = true;
     if (n <= 128) {
         s.scan_cnt = n;
         s.bits = 7;
-    } else {
-        float icn = (P.nf * (1.0f - qh.z) - 1.0f) * 0.5f;
-        float ics = (P.nf * (1.0f + qh.z) - 1.0f) * 0.5f;
-        if (icn < 16.0f) {
-            s.scan_cnt = 64;
-            s.bits = 6;
-        } else if (ics < 16.0f) {
-            s.scan_base = n - 64;
-            s.scan_cnt = 64;
-            s.bits = 6;
-        } else {
-            s.w = lattice_window(P, qh);
-        }
+        return s;
     }
-    return s;
-}
-
-__device__ __forceinline__ int32_t source_index(const Source &s, int slot)
-{
-    return s.scan_cnt ? s.scan_base + slot : window_index(s.w, slot);
+    float icn = (P.nf * (1.0f - qh.z) - 1.0f) * 0.5f;
+    float ics = (P.nf * (1.0f + qh.z) - 1.0f) * 0.5f;
+    s.scan_cnt = 64;
+    s.bits = 6;
+    if (icn < 16.0f) return s;
+    s.b0 = n - 64;
+    if (ics < 16.0f) return s;
+    return lattice_window(P, qh);
 }
 
 // Tier-1 squared distance from the hi parts only.
@@ -429,12 +435,17 @@ __device__ __forceinline__ float dist2_hi(const PointSetK &P, int32_t i, float3 
     return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
 }
 
-// Bound of |dist2_hi - d^2| (hi parts within 2^-24 of q and p per component,
-// one rounding per subtraction, three roundings in the sum of squares).
+// Bound of |dist2_hi - d^2| as a function of the computed d1 = dist2_hi. The
+// hi parts lie within 2^-25 (+ the 2^-37 of the unit hit) of q and p per
+// component, so each difference is off by at most 2^-24 (1 + 2^-12) plus one
+// rounding; squaring and the three roundings of the sum give
+// |d1 - d^2| <= 5u d^2 + 2 sqrt(3) 2^-24 d + 3 * 2^-46 (u = 2^-24), which
+// 2^-21 d1 + 2^-21 sqrt(d1) + 2^-42 exceeds by a factor of two or more in each
+// term (also for d^2 up to d1 + e1, and with the few ulps of rsqrtf).
 __device__ __forceinline__ float tier1_err(float d2)
 {
     float d = d2 * rsqrtf(fmaxf(d2, 0x1p-100f));          // sqrt(d2) to a few ulps
-    return __fmaf_rn(0x1p-21f, d2, __fmaf_rn(0x1p-20f, d, 0x1p-42f));
+    return __fmaf_rn(0x1p-21f, d2, __fmaf_rn(0x1p-21f, d, 0x1p-42f));
 }
 
 template <int K>
@@ -445,43 +456,19 @@ struct TopK {
 };
 using Top5 = TopK<5>;
 
-// Exact ranking in FP64 over the same candidates (rare: an uncertain order).
-__device__ __forceinline__ Top5 knn5_fp64(const PointSetK P, const SphereK S, float3 h, const Source src,
-                                       float3 qh, float3 ql)
-{
-    double q[3];
-    unit_hit_fp64(S, h, q);
-    int32_t idx[5];
-    double dd[5];
-    int cnt = 0;
-    const int32_t n = (int32_t)P.n;
-    const int total = src.scan_cnt ? src.scan_cnt : kWindow;
-    for (int s = 0; s < total; ++s) {
-        int32_t i = source_index(src, s);
-        if (i < 0 || i >= n) continue;
-        double d = dist2_fp64(P, i, q);
-        if (cnt == 5 && !(d < dd[4] || (d == dd[4] && i < idx[4]))) continue;
-        int m = cnt < 5 ? cnt++ : 4;
-        while (m > 0 && (d < dd[m - 1] || (d == dd[m - 1] && i < idx[m - 1]))) {
-            dd[m] = dd[m - 1];
-            idx[m] = idx[m - 1];
-            --m;
-        }
-        dd[m] = d;
-        idx[m] = i;
-    }
-    Top5 r;
-    for (int m = 0; m < 5; ++m) {
-        r.i[m] = m < cnt ? idx[m] : -1;
-        r.d2[m] = m < cnt ? dist2_df(P, idx[m], qh, ql) : 0.0f;
-    }
-    r.cnt = cnt;
-    return r;
-}
-
-// The 5 nearest points of the unit hit (qh + ql) in (distance, index) order,
-// with their double-float squared distances. cnt = min(5, n).
-__device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float3 h, uint32_t *status)
+// The 5 nearest points of the unit hit of h (qh + ql) in (distance, index)
+// order, with their double-float squared distances; cnt = min(5, n). This is
+// the render kernels' fast path: tier 1 and its order certificate, and when
+// that fails a short tier 2 over the tier-1 top 6. When tier 2 cannot settle
+// the order either, `uncertain` is set and the result is meaningless; the
+// render kernel queues the ray for the exact pass (coop_knn5 in a kernel of
+// its own). Neither the exact ranking nor any FP64 code sits in the render
+// kernel: a rarely taken path there costs the common path registers (spills),
+// and run by one lane it holds its warp and CTA for tens of thousands of
+// cycles (FP64 division and square root alone take hundreds of cycles each on
+// this GPU).
+__device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float3 h, uint32_t *status,
+                                     bool &uncertain)
 {
     float3 qh, ql;
     unit_hit_df(S, h, qh, ql);
@@ -490,126 +477,285 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
     const uint32_t mask1 = (1u << src.bits) - 1u;
     constexpr uint32_t kNone = 0xffffffffu;
 
-    // Tier 1: the 7 smallest FP32 keys.
+    // Tier 1: the 7 smallest keys, sorted.
     uint32_t s7[7];
-    if (src.scan_cnt == 0) {
-        uint32_t k[16];
-        if (src.w.interior) {
+    if (src.scan_cnt == 0 && src.interior) {
+        // the common case: 12 window corners, all in range, unrolled
+        uint32_t k[12];
 #pragma unroll
-            for (int s = 0; s < kWindow; ++s) {
-                float dd = dist2_hi(P, LF_DINDEX(window_index(src.w, s), P.n, status, kStatusDebugPoint), qh);
-                k[s] = (__float_as_uint(dd) & ~15u) | (uint32_t)s;
-            }
-        } else {
-#pragma unroll
-            for (int s = 0; s < kWindow; ++s) {
-                int32_t i = window_index(src.w, s);
-                bool ok = (uint32_t)i < (uint32_t)n;
-                float dd = dist2_hi(P, ok ? i : 0, qh);
-                k[s] = ok ? ((__float_as_uint(dd) & ~15u) | (uint32_t)s) : kNone;
-            }
+        for (int j = 0; j < kWindow; ++j) {
+            const uint32_t s = slot5(j);
+            const int32_t i = source_index(src, s);
+            const float dd = dist2_hi(P, LF_DINDEX(i, P.n, status, kStatusDebugPoint), qh);
+            k[j] = (__float_as_uint(dd) & ~15u) | s;
         }
-#pragma unroll
-        for (int s = kWindow; s < 16; ++s) k[s] = kNone;
-        select7_of16(k);
+        select7_of12(k);
 #pragma unroll
         for (int m = 0; m < 7; ++m) s7[m] = k[m];
     } else {
+        // pole and full scans, windows that reach past either end of the index range
 #pragma unroll
         for (int m = 0; m < 7; ++m) s7[m] = kNone;
-        for (int s = 0; s < src.scan_cnt; ++s)
-            insert7(s7, (__float_as_uint(dist2_hi(P, LF_DINDEX(src.scan_base + s, P.n, status, kStatusDebugPoint), qh)) &
-                         ~mask1) | (uint32_t)s);
+        const int total = src.scan_cnt ? src.scan_cnt : kWindow;
+#pragma unroll 1
+        for (int j = 0; j < total; ++j) {
+            const uint32_t s = src.scan_cnt ? (uint32_t)j : slot5(j);
+            const int32_t i = source_index(src, s);
+            if ((uint32_t)i >= (uint32_t)n) continue;
+            insert7(s7, (__float_as_uint(dist2_hi(P, LF_DINDEX(i, P.n, status, kStatusDebugPoint), qh)) & ~mask1) | s);
+        }
     }
 
-    // Bounds of the exact squared distance behind each of the 7 keys: the key
-    // lost its low `bits` bits to the slot, and one FP32 error bound serves
-    // all 7 (tier1_err grows with the distance; taken at the 7th key, and at
-    // 4.5 > any squared chord when that slot is empty).
-    float ub[7], lb[7];
-    const float e7 = tier1_err(fminf(__uint_as_float(s7[6] | mask1), 4.5f));
-#pragma unroll
-    for (int m = 0; m < 7; ++m) {
-        ub[m] = __uint_as_float(s7[m] | mask1) + e7;
-        lb[m] = __uint_as_float(s7[m] & ~mask1) - e7;
-    }
-    // Double-float distances of the tier-1 top 5 (the weights need them).
-    int32_t i5[5];
-    float p5[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        bool ok = s7[m] != kNone;
-        i5[m] = ok ? source_index(src, (int)(s7[m] & mask1)) : 0;
-        p5[m] = dist2_df(P, LF_DINDEX(i5[m], P.n, status, kStatusDebugPoint), qh, ql);
-    }
-    // Order certificate at tier 1: each of the top 6 lies strictly below the
-    // next by more than any FP64 rounding of the ranking distances (2^-40), so
-    // order and membership of the 5 equal those of the exact ranking. Else
-    // tier 2 re-ranks the top 6 in double-float, and FP64 settles the rest.
+    // Order certificate at tier 1. The keys lost their low `bits` bits to the
+    // slot, and one bound e1 serves all of them (tier1_err grows with the
+    // distance; taken at the 6th key, and at 4.5 > any squared chord when that
+    // slot is empty). Each of the top 6 lying below the next by more than
+    // 2^-40 (far above any FP64 rounding of the oracle's distances) makes the
+    // order and the membership of the 5 those of the exact ranking: every
+    // candidate past the 6th has a key, hence a lower bound, at least the 6th's.
+    const float e1 = tier1_err(fminf(__uint_as_float(s7[5] | mask1), 4.5f));
+    const float gap = __fmaf_rn(2.0f, e1, 0x1p-40f);
     bool order1 = true;
 #pragma unroll
     for (int m = 0; m < 5; ++m)
-        if (s7[m + 1] != kNone) order1 &= (lb[m + 1] - ub[m]) > 0x1p-40f;
+        if (s7[m + 1] != kNone)
+            order1 &= __fsub_rn(__uint_as_float(s7[m + 1] & ~mask1), __uint_as_float(s7[m] | mask1)) > gap;
     Top5 r;
     r.cnt = 0;
+    if (order1) {
+        // Double-float distances of the 5 for their weights.
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        bool ok = s7[m] != kNone;
-        r.i[m] = ok ? i5[m] : -1;
-        r.d2[m] = ok ? p5[m] : 0.0f;
-        r.cnt += ok ? 1 : 0;
+        for (int m = 0; m < 5; ++m) {
+            const bool ok = s7[m] != kNone;
+            const int32_t i = ok ? source_index(src, s7[m] & mask1) : 0;
+            r.i[m] = ok ? i : -1;
+            r.d2[m] = ok ? dist2_df(P, LF_DINDEX(i, P.n, status, kStatusDebugPoint), qh, ql) : 0.0f;
+            r.cnt += ok ? 1 : 0;
+        }
+        return r;
     }
-    if (!order1) {
-        // membership: the 5th upper bound below the 7th lower bound
-        bool exact = s7[6] == kNone || lb[6] > ub[4];
+    {
+        // Double-float distances of the tier-1 top 5.
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const bool ok = s7[m] != kNone;
+            const int32_t i = ok ? source_index(src, s7[m] & mask1) : 0;
+            r.i[m] = ok ? i : -1;
+            r.d2[m] = ok ? dist2_df(P, LF_DINDEX(i, P.n, status, kStatusDebugPoint), qh, ql) : 0.0f;
+            r.cnt += ok ? 1 : 0;
+        }
+        // Tier 2: the top 6 in double-float, sorted, when the tier-1 bounds put
+        // the true 5 nearest among them (the 5th's upper bound below the 7th's
+        // lower bound, with the error bound taken at the 7th key). Accepted when
+        // every consecutive gap of the 6 exceeds the tier-2 error (2^-21 relative
+        // per distance, 2^-20 for the 3 slot bits of the keys, 2^-40 absolute);
+        // otherwise the hit is left to the exact pass.
+        const float e7 = tier1_err(fminf(__uint_as_float(s7[6] | mask1), 4.5f));
+        bool ok2 = s7[6] == kNone ||
+                   __fsub_rn(__uint_as_float(s7[6] & ~mask1), e7) > __fadd_rn(__uint_as_float(s7[4] | mask1), e7);
+        const int32_t i5 = s7[5] != kNone ? source_index(src, s7[5] & mask1) : 0;
+        const float d5 = dist2_df(P, LF_DINDEX(i5, P.n, status, kStatusDebugPoint), qh, ql);
         uint32_t k6[6];
-        int32_t id6[6];
-        float dd6[6];
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
-            bool ok = s7[m] != kNone;
-            int32_t i = m < 5 ? i5[m] : (ok ? source_index(src, (int)(s7[m] & mask1)) : 0);
-            id6[m] = i;
-            dd6[m] = m < 5 ? p5[m] : dist2_df(P, i, qh, ql);
-            k6[m] = ok ? ((__float_as_uint(dd6[m]) & ~7u) | (uint32_t)m) : kNone;
+            const float dm = m < 5 ? r.d2[m] : d5;
+            k6[m] = s7[m] != kNone ? ((__float_as_uint(dm) & ~7u) | (uint32_t)m) : kNone;
         }
         sort6(k6);
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             if (k6[m + 1] != kNone) {
-                float a = __uint_as_float(k6[m] & ~7u), b = __uint_as_float(k6[m + 1] & ~7u);
-                exact &= (b - a) > __fmaf_rn(0x1p-18f, b, 0x1p-40f);
+                const float a = __uint_as_float(k6[m] & ~7u), b = __uint_as_float(k6[m + 1] & ~7u);
+                ok2 &= (b - a) > __fmaf_rn(0x1p-18f, b, 0x1p-40f);
             }
         }
-        if (exact) {
-            r.cnt = 0;
+        if (!ok2) {
+            uncertain = true;
+            return r;
+        }
+        // the order of the 5 by their tier-2 distances
+        Top5 t;
+        t.cnt = r.cnt;
 #pragma unroll
-            for (int m = 0; m < 5; ++m) {
-                bool ok = k6[m] != kNone;
-                int sl = (int)(k6[m] & 7u);
-                int32_t i = id6[0];
-                float dd = dd6[0];
+        for (int m = 0; m < 5; ++m) {
+            const int sl = (int)(k6[m] & 7u);
+            int32_t i = sl == 5 ? i5 : r.i[0];
+            float dd = sl == 5 ? d5 : r.d2[0];
 #pragma unroll
-                for (int c = 1; c < 6; ++c) {
-                    i = (sl == c) ? id6[c] : i;
-                    dd = (sl == c) ? dd6[c] : dd;
-                }
-                r.i[m] = ok ? i : -1;
-                r.d2[m] = ok ? dd : 0.0f;
-                r.cnt += ok ? 1 : 0;
+            for (int c = 1; c < 5; ++c) {
+                i = sl == c ? r.i[c] : i;
+                dd = sl == c ? r.d2[c] : dd;
             }
-        } else {
-            r = knn5_fp64(P, S, h, src, qh, ql);
+            t.i[m] = k6[m] != kNone ? i : -1;
+            t.d2[m] = k6[m] != kNone ? dd : 0.0f;
+        }
+        return t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative exact ranking (the rare hits whose tier-1 order was not
+// certain). All 32 lanes of a warp call it with the same hit h; lane l takes
+// candidates l, l + 32, l + 64, l + 96 of the source, each lane computes its
+// candidates' squared distances in double-float (tier 2), and six rounds of a
+// warp-wide minimum by (distance, index) pick the nearest in order. The order
+// is accepted when each of the top 6 lies below the next by more than the
+// tier-2 error; otherwise the same rounds run on FP64 distances computed in
+// the FP64 definition's operation order (ties to the smaller index). The
+// latency is that of a handful of loads and shuffles, not of a long serial
+// path in one lane.
+// ---------------------------------------------------------------------------
+
+// Squared distance |q - p|^2 in double-float (q = qh + ql, p = hi + lo of
+// point i): each difference exact up to 2^-47 (two_sum of the hi parts plus
+// the lo parts), squares and sums as double-float products and sums.
+__device__ __forceinline__ df dist2_dd(const PointSetK &P, int32_t i, float3 qh, float3 ql)
+{
+    const float4 a = __ldg(P.hi + i);
+    const float4 b = __ldg(P.lo + i);
+    const float qv[3] = {qh.x, qh.y, qh.z}, lv[3] = {ql.x, ql.y, ql.z};
+    const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z};
+    df acc{0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const df s = two_sum(qv[k], -av[k]);
+        const df dx = fast_two_sum(s.h, __fadd_rn(s.l, __fsub_rn(lv[k], bv[k])));
+        acc = df_add(acc, df_mul(dx, dx));
+    }
+    return acc;
+}
+
+// Bound of |dist2_dd - d^2| for the exact unit hit and point: the unit hit's
+// own error (2^-37 per component at worst) and the differences' 2^-47 give
+// 2 sqrt(3) (2^-37 + 2^-47) d, the double-float squares and sums 2^-44 d^2;
+// this exceeds both by a factor of two.
+__device__ __forceinline__ float tier2_err(float d2)
+{
+    const float d = d2 * rsqrtf(fmaxf(d2, 0x1p-100f));
+    return __fmaf_rn(0x1p-43f, d2, __fmaf_rn(0x1p-34f, d, 0x1p-70f));
+}
+
+// (a, ia) < (b, ib) for double-float distances, ties to the smaller index.
+__device__ __forceinline__ bool dd_less(df a, int32_t ia, df b, int32_t ib)
+{
+    return a.h < b.h || (a.h == b.h && (a.l < b.l || (a.l == b.l && ia < ib)));
+}
+
+__device__ __forceinline__ Top5 coop_knn5(const PointSetK &P, const SphereK &S, float3 h)
+{
+    constexpr int kPer = 4;                       // candidates per lane (scans have at most 128)
+    constexpr int32_t kNoIdx = 0x7fffffff;
+    const unsigned full = 0xffffffffu;
+    const int lane = (int)(threadIdx.x & 31u);
+    float3 qh, ql;
+    unit_hit_df(S, h, qh, ql);
+    const int32_t n = (int32_t)P.n;
+    const Source src = candidate_source(P, qh);
+    const int total = src.scan_cnt ? src.scan_cnt : kWindow;
+    df kd[kPer];
+    int32_t ki[kPer];
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+        kd[c] = df{INFINITY, 0.0f};
+        ki[c] = kNoIdx;
+        if (32 * c >= total) continue;            // warp-uniform: windows fill lanes 0..11 only
+        const int j = lane + 32 * c;
+        const int32_t i = j < total ? source_index(src, src.scan_cnt ? (uint32_t)j : slot5(j)) : -1;
+        if ((uint32_t)i < (uint32_t)n) {
+            kd[c] = dist2_dd(P, i, qh, ql);
+            ki[c] = i;
         }
     }
+    // six rounds of a warp-wide minimum; the lane holding the winner retires it
+    df wd6[6];
+    int32_t wi6[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        df bd = kd[0];
+        int32_t bi = ki[0];
+#pragma unroll
+        for (int c = 1; c < kPer; ++c)
+            if (dd_less(kd[c], ki[c], bd, bi)) {
+                bd = kd[c];
+                bi = ki[c];
+            }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const df od{__shfl_xor_sync(full, bd.h, o), __shfl_xor_sync(full, bd.l, o)};
+            const int32_t oi = __shfl_xor_sync(full, bi, o);
+            if (dd_less(od, oi, bd, bi)) {
+                bd = od;
+                bi = oi;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kPer; ++c)
+            if (ki[c] == bi) {
+                kd[c] = df{INFINITY, 0.0f};
+                ki[c] = kNoIdx;
+            }
+        wd6[r] = bd;
+        wi6[r] = bi;
+    }
+    bool exact = true;
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        if (m < r.cnt && (uint32_t)r.i[m] >= (uint32_t)n) {   // impossible by construction; recorded, never trapped
-            atomicOr(status, 1u);
-            r.i[m] = 0;
+        if (wi6[m + 1] != kNoIdx) {
+            const float g = __fadd_rn(__fsub_rn(wd6[m + 1].h, wd6[m].h), __fsub_rn(wd6[m + 1].l, wd6[m].l));
+            exact &= g > 2.0f * tier2_err(wd6[m + 1].h);
         }
     }
-    return r;
+    if (!exact) {
+        // FP64 in the definition's operation order, over the same candidates
+        double q[3];
+        unit_hit_fp64(S, h, q);
+        double kq[kPer];
+#pragma unroll
+        for (int c = 0; c < kPer; ++c) {
+            const int j = lane + 32 * c;
+            const int32_t i = j < total ? source_index(src, src.scan_cnt ? (uint32_t)j : slot5(j)) : -1;
+            const bool ok = (uint32_t)i < (uint32_t)n;
+            kq[c] = ok ? dist2_fp64(P, i, q) : INFINITY;
+            ki[c] = ok ? i : kNoIdx;
+        }
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            double bd = kq[0];
+            int32_t bi = ki[0];
+#pragma unroll
+            for (int c = 1; c < kPer; ++c)
+                if (kq[c] < bd || (kq[c] == bd && ki[c] < bi)) {
+                    bd = kq[c];
+                    bi = ki[c];
+                }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const double od = __shfl_xor_sync(full, bd, o);
+                const int32_t oi = __shfl_xor_sync(full, bi, o);
+                if (od < bd || (od == bd && oi < bi)) {
+                    bd = od;
+                    bi = oi;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kPer; ++c)
+                if (ki[c] == bi) {
+                    kq[c] = INFINITY;
+                    ki[c] = kNoIdx;
+                }
+            wi6[r] = bi;
+        }
+    }
+    Top5 res;
+    res.cnt = 0;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const bool ok = wi6[m] != kNoIdx;
+        res.i[m] = ok ? wi6[m] : -1;
+        res.d2[m] = ok ? dist2_df(P, wi6[m], qh, ql) : 0.0f;
+        res.cnt += ok ? 1 : 0;
+    }
+    return res;
 }
 
 // ---------------------------------------------------------------------------
@@ -628,14 +774,16 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
 // ---------------------------------------------------------------------------
 constexpr int kWindow9 = 25;
 
-__device__ __forceinline__ int32_t window_index25(const Window &w, int slot)
+// The 5x5 corners around the rounded corner c = b0 + G0 + G1 (the block is
+// invariant under the quadrant's quarter turns of the basis).
+__device__ __forceinline__ int32_t window_index25(const Source &s, int slot)
 {
-    return w.base + (slot / 5 - 2) * w.F0 + (slot % 5 - 2) * w.F1;
+    return s.b0 + (slot / 5 - 1) * s.G0 + (slot % 5 - 1) * s.G1;
 }
 
 __device__ __forceinline__ int32_t source_index9(const Source &s, int slot)
 {
-    return s.scan_cnt ? s.scan_base + slot : window_index25(s.w, slot);
+    return s.scan_cnt ? s.b0 + slot : window_index25(s, slot);
 }
 
 template <int N>
@@ -756,14 +904,14 @@ __device__ __forceinline__ TopK<9> knn9(const PointSetK &P, const SphereK &S, fl
     if (src.scan_cnt == 0) {
 #pragma unroll 5
         for (int s = 0; s < kWindow9; ++s) {
-            int32_t i = window_index25(src.w, s);
+            int32_t i = window_index25(src, s);
             bool ok = (uint32_t)i < (uint32_t)n;
             float dd = dist2_hi(P, ok ? i : 0, qh);
             insert_sorted(s10, ok ? ((__float_as_uint(dd) & ~mask1) | (uint32_t)s) : kNone);
         }
     } else {
         for (int s = 0; s < src.scan_cnt; ++s)
-            insert_sorted(s10, (__float_as_uint(dist2_hi(P, src.scan_base + s, qh)) & ~mask1) | (uint32_t)s);
+            insert_sorted(s10, (__float_as_uint(dist2_hi(P, src.b0 + s, qh)) & ~mask1) | (uint32_t)s);
     }
 
     // one tier-1 error bound for all keys, taken at the 10th (4.5 for an empty slot)

@@ -65,6 +65,14 @@ struct PointSetK {
     float inv_sigma;
 };
 
+// Argument checks and view set-up shared by the entry points (lf_abi.cu): a
+// failed check sets the calling thread's lf_last_error() message.
+lf_status check_desc(const lf_table_desc *d);
+lf_status check_launch(const lf_launch *c);
+lf_status check_views(const lf_view *views, uint32_t n);
+ViewK camera_of(const lf_view &w);                  // the camera only (no tiling, no miss constants)
+ViewK view_params(const lf_view &w, const lf_launch &L, double R, const double O[3]);
+
 }  // namespace lfk
 
 struct lf_table {
@@ -78,7 +86,7 @@ struct lf_table {
     void *owned_texels;              // non-NULL if the library owns the copy
     float *owned_scales;
     float4 *points;                  // [2M + 2N]: origins hi, lo, then directions hi, lo
-    uint32_t *scratch;               // [0] status word, [1] tile queue, [2] finished CTAs
+    uint32_t *scratch;               // device words and the queue of deferred rays (layout: lf_kernels.h)
     lfk::SphereK sphere;
     lfk::PointSetK po, pd;
     lf_launch launch;

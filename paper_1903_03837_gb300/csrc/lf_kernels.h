@@ -13,6 +13,14 @@ constexpr int kLargeViews = 64;    // batches are split into launches of <= 64 v
 constexpr int kMaxBlock = 256;     // threads per CTA (tile_w * tile_h)
 constexpr uint32_t kStripTiles = 4;
 
+// Device words of a table or of a no-allocation render: [0] status, [1] tile
+// queue, [2] finished render CTAs, [3] finished fixup CTAs, bytes 16..23 the
+// count of queued rays; the queued rays follow at byte kWordsBytes.
+constexpr uint32_t kWordsBytes = 256;
+constexpr uint32_t kDeferCap = 1u << 18;         // queued rays a table holds per launch
+constexpr unsigned kFixupCtas = 304, kFixupThreads = 256;
+constexpr uint32_t kFixupWarps = kFixupThreads / 32;
+
 struct RenderParamsBase {
     SphereK sphere;
     PointSetK po, pd;
@@ -27,6 +35,14 @@ struct RenderParamsBase {
     const float *grad_out;         // backward: [P][C]
     float *grad;                   // backward: [M][N][C]
     uint32_t *status, *queue, *done;
+    // Rays whose fast-path order was not certain: the render kernel queues
+    // them here and the fixup kernel that follows it on the stream renders
+    // them (more than defer_cap in one launch: the fixup renders every ray).
+    unsigned long long *defer_count;   // rays queued in this launch (reset by the fixup kernel)
+    uint32_t *defer_done;              // fixup CTAs finished
+    unsigned long long *defer_items;   // [defer_cap]: view << 32 | y << 16 | x
+    uint32_t defer_cap;
+    uint64_t total_pixels;             // pixels of all views of the launch
     uint32_t n_views, total_tiles;
     uint32_t tile_w, tile_h, warp_w, order, persistent;
     uint32_t tw_log, th_log, ww_log;   // log2 of tile_w, tile_h, warp_w

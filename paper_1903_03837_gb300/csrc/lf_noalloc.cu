@@ -11,18 +11,18 @@
 // holds until the process exits.
 //
 // Layout of the array: the hi/lo point caches of both SF sets (M + N points,
-// 32 B each) followed by 256 B of words (status, tile queue, finished CTAs).
-// Every call rebuilds the point caches and clears the words on its stream, so
-// the array only ever holds the last call's contents; calls that overlap on
-// the GPU (different streams, or another thread) race on it.
+// 32 B each), then 256 B of words (status, tile queue, finished CTAs, the
+// count of rays queued for the exact fixup pass), then the queue itself
+// (kNoAllocDeferCap entries of 8 B). Every call rebuilds the point caches and
+// clears the words on its stream, so the array only ever holds the last
+// call's contents; calls that overlap on the GPU (different streams, or
+// another thread) race on it.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
-#include <string>
 
 #include "lf_kernels.h"
 #include "lumipath.h"
@@ -30,12 +30,11 @@
 namespace {
 
 constexpr uint64_t kNoAllocMaxPoints = LF_NOALLOC_MAX_POINTS;     // M + N
-constexpr uint64_t kWordsFloat4 = 16;                                // 256 B of words
+constexpr uint64_t kWordsFloat4 = lfk::kWordsBytes / 16;             // 256 B of words
+constexpr uint32_t kNoAllocDeferCap = LF_NOALLOC_MAX_DEFERRED;       // queued rays per launch
+constexpr uint64_t kQueueFloat4 = kNoAllocDeferCap / 2;              // 8 B per queued ray
 
-static __device__ __align__(256) float4 g_lf_noalloc_scratch[2 * kNoAllocMaxPoints + kWordsFloat4];
-
-std::mutex g_addr_mu;
-void *g_addr[256];          // device address of the array, per device ordinal
+static __device__ __align__(256) float4 g_lf_noalloc_scratch[2 * kNoAllocMaxPoints + kWordsFloat4 + kQueueFloat4];
 
 lf_status na_fail(lf_status s, const char *fmt, ...)
 {
@@ -49,21 +48,17 @@ lf_status na_fail(lf_status s, const char *fmt, ...)
 }
 
 // Host code must not use g_lf_noalloc_scratch directly: on the host it names a
-// stand-in object, not device memory. Look up its device address once per
-// device, with that device current.
-lf_status scratch_address(int dev, float4 **out)
+// stand-in object, not device memory. Its device address is looked up on every
+// call, with the caller's device current: the lookup allocates nothing, and an
+// address kept from an earlier call could belong to a context that has since
+// been torn down (cudaDeviceReset), where it would no longer be valid.
+lf_status scratch_address(float4 **out)
 {
-    if (dev < 0 || dev >= 256) return na_fail(LF_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_addr_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_lf_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return na_fail(LF_ERR_CUDA, "cudaGetSymbolAddress of the no-allocation scratch: %s",
-                           cudaGetErrorString(e));
-        g_addr[dev] = p;
-    }
-    *out = (float4 *)g_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_lf_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return na_fail(LF_ERR_CUDA, "cudaGetSymbolAddress of the no-allocation scratch: %s", cudaGetErrorString(e));
+    *out = (float4 *)p;
     return LF_OK;
 }
 
@@ -74,25 +69,12 @@ lf_status launch_views(const lfk::RenderParamsBase &base, const lf_launch &L, in
     static thread_local lfk::RenderParams<MAXV> p;
     static_cast<lfk::RenderParamsBase &>(p) = base;
     uint64_t tiles = 0;
+    p.total_pixels = 0;
     for (uint32_t v = 0; v < nv; ++v) {
-        lfk::ViewK &k = p.views[v];
-        const lf_view &w = views[v];
-        for (int i = 0; i < 3; ++i) {
-            k.eye[i] = w.eye[i];
-            k.right[i] = w.right[i];
-            k.up[i] = w.up[i];
-            k.fwd[i] = w.forward[i];
-        }
-        k.tan_x = w.tan_half_x;
-        k.tan_y = w.tan_half_y;
-        k.width = w.width;
-        k.height = w.height;
-        k.out_offset = w.out_offset;
-        k.tiles_x = (w.width + L.tile_w - 1) / L.tile_w;
-        k.tiles_y = (w.height + L.tile_h - 1) / L.tile_h;
-        lfk::fill_view_miss_consts(k, d->radius, d->center);
+        p.views[v] = lfk::view_params(views[v], L, d->radius, d->center);
         p.tile_prefix[v] = (uint32_t)tiles;
-        tiles += (uint64_t)k.tiles_x * k.tiles_y;
+        tiles += (uint64_t)p.views[v].tiles_x * p.views[v].tiles_y;
+        p.total_pixels += (uint64_t)views[v].width * views[v].height;
     }
     if (tiles >= (1ull << 31)) return na_fail(LF_ERR_INVALID_ARG, "too many tiles in one launch");
     p.tile_prefix[nv] = (uint32_t)tiles;
@@ -125,29 +107,18 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
                             float *out_dev, int32_t *idx_dev, void *stream)
 {
     lfk::set_last_error("");
-    if (!d || !radiance_dev || !views || !out_dev) return na_fail(LF_ERR_INVALID_ARG, "NULL argument");
-    if (!(std::isfinite(d->radius) && d->radius > 0.0))
-        return na_fail(LF_ERR_INVALID_ARG, "radius must be finite and > 0");
-    for (int k = 0; k < 3; ++k)
-        if (!std::isfinite(d->center[k])) return na_fail(LF_ERR_INVALID_ARG, "center must be finite");
+    lf_status s = lfk::check_desc(d);
+    if (s != LF_OK) return s;
+    if (!radiance_dev || !out_dev) return na_fail(LF_ERR_INVALID_ARG, "NULL argument");
     const uint32_t M = d->n_origins, N = d->n_directions, C = d->channels;
-    if (M == 0 || N == 0) return na_fail(LF_ERR_INVALID_ARG, "point counts must be >= 1");
     if ((uint64_t)M + N > kNoAllocMaxPoints)
         return na_fail(LF_ERR_INVALID_ARG,
                        "M + N = %llu exceeds the no-allocation scratch limit of %llu points",
                        (unsigned long long)M + N, (unsigned long long)kNoAllocMaxPoints);
-    if (C != 3 && C != 4) return na_fail(LF_ERR_INVALID_ARG, "channels must be 3 or 4");
-    if (d->dtype != LF_DTYPE_F32 && d->dtype != LF_DTYPE_F16 && d->dtype != LF_DTYPE_E4M3)
-        return na_fail(LF_ERR_INVALID_ARG, "unknown dtype %d", d->dtype);
     const bool quant = d->dtype != LF_DTYPE_F32;
     if (quant && (C != 4 || !row_scales_dev))
         return na_fail(LF_ERR_INVALID_ARG, "F16/E4M3 tables need 4 channels and row scales here");
-    if (d->k_nearest != 0 && d->k_nearest != 1 && d->k_nearest != 5)
-        return na_fail(LF_ERR_UNSUPPORTED, "1 or 5 neighbours per hit here (9: lf_render)");
-    if (d->flags & ~(LF_TABLE_BORROW | LF_TABLE_UPPER_HEMISPHERE))
-        return na_fail(LF_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
-    if ((d->flags & LF_TABLE_UPPER_HEMISPHERE) && M < 2)
-        return na_fail(LF_ERR_INVALID_ARG, "an upper-hemisphere table needs M >= 2");
+    if (d->k_nearest == 9) return na_fail(LF_ERR_UNSUPPORTED, "1 or 5 neighbours per hit here (9: lf_render)");
     {
         // natural alignment of the vector accesses (a misaligned pointer is an argument error)
         const uintptr_t ta = !quant ? (C == 4 ? 16 : 8) : (d->dtype == LF_DTYPE_F16 ? 8 : 4);
@@ -156,40 +127,25 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
             ((uintptr_t)idx_dev & 7u) || ((uintptr_t)row_scales_dev & 3u))
             return na_fail(LF_ERR_INVALID_ARG, "misaligned table, scale, image or index buffer");
     }
-    if (n_views == 0 || n_views > 65536) return na_fail(LF_ERR_INVALID_ARG, "n_views must be in [1, 65536]");
-    for (uint32_t v = 0; v < n_views; ++v) {
-        const lf_view &w = views[v];
-        if (w.width == 0 || w.height == 0 || w.width > 65536 || w.height > 65536)
-            return na_fail(LF_ERR_INVALID_ARG, "view %u: size out of range", v);
-        bool fin = std::isfinite(w.tan_half_x) && std::isfinite(w.tan_half_y);
-        for (int k = 0; k < 3; ++k)
-            fin = fin && std::isfinite(w.eye[k]) && std::isfinite(w.right[k]) && std::isfinite(w.up[k]) &&
-                  std::isfinite(w.forward[k]);
-        if (!fin) return na_fail(LF_ERR_INVALID_ARG, "view %u: non-finite camera", v);
-        uint64_t end = w.out_offset + (uint64_t)w.width * w.height;
-        if (end < w.out_offset || end > (1ull << 40)) return na_fail(LF_ERR_INVALID_ARG, "view %u: output overflows", v);
-    }
-    lf_launch L;
+    s = lfk::check_views(views, n_views);
+    if (s != LF_OK) return s;
+    lf_launch L = {16, 16, 8, 0, 0, 0};
     if (launch) {
+        s = lfk::check_launch(launch);
+        if (s != LF_OK) return s;
         L = *launch;
-        uint32_t ww = L.warp_w;
-        bool ok = (ww == 1 || ww == 2 || ww == 4 || ww == 8 || ww == 16 || ww == 32) && L.tile_w && L.tile_h &&
-                  !(L.tile_w & (L.tile_w - 1)) && !(L.tile_h & (L.tile_h - 1)) &&
-                  L.tile_w % ww == 0 && L.tile_h % (32 / ww) == 0 && L.tile_w * L.tile_h <= (uint32_t)lfk::kMaxBlock &&
-                  L.order <= 1 && L.persistent <= 1 && L.ctas_per_sm <= 64;
-        if (!ok) return na_fail(LF_ERR_INVALID_ARG, "inconsistent launch shape");
-    } else {
-        L = {16, 16, 8, 0, 0, 0};
     }
 
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(LF_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     float4 *base = nullptr;
-    lf_status s = scratch_address(dev, &base);
+    s = scratch_address(&base);
     if (s != LF_OK) return s;
     int sm_count = 0;
-    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || sm_count <= 0)
+        return na_fail(LF_ERR_CUDA, "SM count of device %d: %s", dev, cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)stream;
     float4 *po_hi = base, *po_lo = base + M, *pd_hi = base + 2 * (uint64_t)M, *pd_lo = pd_hi + N;
     uint32_t *words = reinterpret_cast<uint32_t *>(base + 2 * kNoAllocMaxPoints);
@@ -213,6 +169,10 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
     b.status = words;
     b.queue = words + 1;
     b.done = words + 2;
+    b.defer_done = words + 3;
+    b.defer_count = reinterpret_cast<unsigned long long *>(words + 4);
+    b.defer_items = reinterpret_cast<unsigned long long *>(base + 2 * kNoAllocMaxPoints + kWordsFloat4);
+    b.defer_cap = kNoAllocDeferCap;
     b.tile_w = L.tile_w;
     b.tile_h = L.tile_h;
     b.warp_w = L.warp_w;
@@ -232,6 +192,26 @@ lf_status lf_render_noalloc(const lf_table_desc *d, const void *radiance_dev, co
         uint32_t nv = n_views - v0 < (uint32_t)lfk::kLargeViews ? n_views - v0 : (uint32_t)lfk::kLargeViews;
         s = launch_views<lfk::kLargeViews>(b, L, kind, sm_count, views + v0, nv, d, st);
         if (s != LF_OK) return s;
+    }
+    return LF_OK;
+}
+
+lf_status lf_noalloc_sync_status(void *stream)
+{
+    lfk::set_last_error("");
+    float4 *base = nullptr;
+    lf_status s = scratch_address(&base);
+    if (s != LF_OK) return s;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return na_fail(LF_ERR_CUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    uint32_t *words = reinterpret_cast<uint32_t *>(base + 2 * kNoAllocMaxPoints);
+    uint32_t w = 0;
+    e = cudaMemcpy(&w, words, sizeof w, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return na_fail(LF_ERR_CUDA, "status read: %s", cudaGetErrorString(e));
+    if (w) {
+        e = cudaMemset(words, 0, sizeof w);
+        if (e != cudaSuccess) return na_fail(LF_ERR_CUDA, "status clear: %s", cudaGetErrorString(e));
+        return na_fail(LF_ERR_DEVICE_CHECK, "device check failed (status word 0x%x)", w);
     }
     return LF_OK;
 }

@@ -60,46 +60,71 @@ __device__ __forceinline__ void pixel_of(const RenderParamsBase &p, uint32_t tx,
     py = (ty << p.th_log) + ((warp >> wx_log) << (5u - p.ww_log)) + (lane >> p.ww_log);
 }
 
-// Indices and normalised weights of one ray (K = 5 or 9 neighbours per hit);
-// false for a miss.
+// Weights of one set's neighbours r (set 0: origins, 1: directions) by the
+// sampling mode; false when the ray is masked (an upper-hemisphere table with
+// no stored origin neighbour).
 template <int K>
-__device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const ViewK &v, uint32_t px,
-                                            uint32_t py, int32_t (&io)[K], int32_t (&jd)[K], float (&wo)[K],
-                                            float (&wd)[K])
+__device__ __forceinline__ bool set_weights(const RenderParamsBase &p, int s, float inv_sigma, TopK<K> &r,
+                                            float (&w)[K])
+{
+    if (p.nearest_only) {
+        // nearest sampling: the nearest point alone (Section 2, Fig. 2)
+        if (s == 0 && p.rows_stored && (uint32_t)r.i[0] >= p.rows_stored) return false;
+#pragma unroll
+        for (int m = 0; m < K; ++m) w[m] = m == 0 ? 1.0f : 0.0f;
+#pragma unroll
+        for (int m = 1; m < K; ++m) r.i[m] = -1;
+        return true;
+    }
+    if (s == 0 && p.rows_stored) return tent_weights_kept(r.d2, r.i, r.cnt, inv_sigma, p.rows_stored, w);
+    tent_weights(r.d2, r.cnt, inv_sigma, w);
+    return true;
+}
+
+__device__ __forceinline__ PointSetK point_set(const RenderParamsBase &p, int s)
+{
+    PointSetK P;
+    P.hi = s ? p.pd.hi : p.po.hi;
+    P.lo = s ? p.pd.lo : p.po.lo;
+    P.n = s ? p.pd.n : p.po.n;
+    P.nf = s ? p.pd.nf : p.po.nf;
+    P.inv_sigma = s ? p.pd.inv_sigma : p.po.inv_sigma;
+    return P;
+}
+
+// Indices and normalised weights of one ray of unit direction d (K = 5 or 9
+// neighbours per hit); false for a miss. With five neighbours, a set whose tier-1 order was not
+// certain sets bit s of `pend` and leaves its samples empty; resolve_pending
+// fills them in once the warp has reconverged.
+template <int K>
+__device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const ViewK &v, float3 d,
+                                            int32_t (&io)[K], int32_t (&jd)[K], float (&wo)[K],
+                                            float (&wd)[K], uint32_t &pend)
 {
     // The origin set's indices and weights wait in shared memory (one slot per
     // thread, no synchronisation) while the direction set is searched: 2K
     // fewer live registers across the second search.
     __shared__ int s_stash[2 * K * kMaxBlock];
-    float3 d = camera_dir(v, px, py);
     float3 ho, hd;
     if (!intersect_sphere(p.sphere, v.eye, d, ho, hd)) return false;
     // One copy of the index step serves both sets (instruction-cache footprint).
 #pragma unroll 1
     for (int s = 0; s < 2; ++s) {
-        PointSetK P;
-        P.hi = s ? p.pd.hi : p.po.hi;
-        P.lo = s ? p.pd.lo : p.po.lo;
-        P.n = s ? p.pd.n : p.po.n;
-        P.nf = s ? p.pd.nf : p.po.nf;
-        P.inv_sigma = s ? p.pd.inv_sigma : p.po.inv_sigma;
+        const PointSetK P = point_set(p, s);
         TopK<K> r;
+        bool unc = false;
         if constexpr (K == 9)
             r = knn9(P, p.sphere, s ? hd : ho, p.status);
         else
-            r = knn5(P, p.sphere, s ? hd : ho, p.status);
+            r = knn5(P, p.sphere, s ? hd : ho, p.status, unc);
         float w[K];
-        if (p.nearest_only) {
-            // nearest sampling: the nearest point alone (Section 2, Fig. 2)
-            if (s == 0 && p.rows_stored && (uint32_t)r.i[0] >= p.rows_stored) return false;
+        if (unc) {
+            pend |= 1u << s;
 #pragma unroll
-            for (int m = 0; m < K; ++m) w[m] = m == 0 ? 1.0f : 0.0f;
-#pragma unroll
-            for (int m = 1; m < K; ++m) r.i[m] = -1;
-        } else if (s == 0 && p.rows_stored) {
-            if (!tent_weights_kept(r.d2, r.i, r.cnt, P.inv_sigma, p.rows_stored, w)) return false;
-        } else {
-            tent_weights(r.d2, r.cnt, P.inv_sigma, w);
+            for (int m = 0; m < K; ++m) w[m] = 0.0f;
+        } else if (!set_weights<K>(p, s, P.inv_sigma, r, w)) {
+            pend = 0;
+            return false;
         }
         if (s == 0) {
 #pragma unroll
@@ -121,6 +146,18 @@ __device__ __forceinline__ bool ray_samples(const RenderParamsBase &p, const Vie
         wo[m] = __int_as_float(s_stash[(K + m) * kMaxBlock + threadIdx.x]);
     }
     return true;
+}
+
+// Queues ray (view vi, pixel px, py) for the fixup kernel; bit s of pend marks
+// a set whose search was not certain. When the queue is full the count still
+// grows past defer_cap, which tells the fixup kernel to render every ray.
+__device__ __forceinline__ void defer_push(const RenderParamsBase &p, uint32_t vi, uint32_t px, uint32_t py,
+                                           uint32_t pend)
+{
+    const unsigned long long slot = atomicAdd(p.defer_count, 1ull);
+    if (slot < p.defer_cap)
+        p.defer_items[slot] = ((unsigned long long)pend << 48) | ((unsigned long long)vi << 32) |
+                              ((unsigned long long)py << 16) | px;
 }
 
 // The samples of one ray from the indices a forward pass wrote for it (idx_in:
@@ -218,70 +255,12 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
     return *reinterpret_cast<float2 *>(&rd);
 }
 
-template <int DT, int K, bool F16>
-__device__ __forceinline__ void render_ray(const RenderParamsBase &p, const ViewK &v, uint32_t px,
-                                           uint32_t py)
+// Image and index output of one ray.
+template <int K, bool F16>
+__device__ __forceinline__ void store_ray(const RenderParamsBase &p, const ViewK &v, uint32_t px, uint32_t py,
+                                          float4 acc, const int32_t (&io)[K], const int32_t (&jd)[K])
 {
-    // initialised even though every path writes them before use: measured 1.6%
-    // faster than leaving them undefined on the miss path
-    int32_t io[K], jd[K];
-    float wo[K], wd[K];
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-        io[m] = jd[m] = -1;
-        wo[m] = wd[m] = 0.0f;
-    }
-    float2 acc_xy = make_float2(0.f, 0.f), acc_zw = make_float2(0.f, 0.f);
-    bool hit = !certain_miss(v, px, py) && ray_samples(p, v, px, py, io, jd, wo, wd);
-    if (hit) {
-        // All K x K taps in every mode: with nearest sampling the other 24 have
-        // weight 0 and index -1 (row 0, texel 0, an L1 hit), which costs less
-        // than a second copy of the loop. The 81 taps of K = 9 keep the outer
-        // loop rolled (instruction-cache footprint).
-#pragma unroll(K == 5 ? 5 : 1)
-        for (int a = 0; a < K; ++a) {
-            // origin neighbour a by a select chain: with the loop rolled (K = 9) a
-            // run-time index would move the arrays to local memory; unrolled (K = 5)
-            // the chain folds away
-            int32_t ia = io[0];
-            float wa = wo[0];
-#pragma unroll
-            for (int m = 1; m < K; ++m) {
-                ia = (a == m) ? io[m] : ia;
-                wa = (a == m) ? wo[m] : wa;
-            }
-            // Nine neighbours: the tent gives the outer ones weight 0 almost always;
-            // their taps are skipped (a branch that whole warps take together).
-            if constexpr (K == 9) {
-                if (wa == 0.0f) continue;
-            }
-            // a missing or unstored neighbour has weight 0 and reads row 0
-            int32_t i = (uint32_t)ia < p.rows_valid ? ia : 0;
-            float s = wa;
-            if constexpr (DT == kF16C4 || DT == kE4M3C4) s *= __ldg(p.scales + i);
-            size_t row = (size_t)i * p.N;
-            float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int b = 0; b < K; ++b) {
-                if constexpr (K == 9) {
-                    if (wd[b] == 0.0f) continue;
-                }
-                float4 t = texel<DT>(p.texels, LF_DINDEX(row + (uint32_t)max(jd[b], 0), (uint64_t)p.rows_valid * p.N,
-                                                          p.status, kStatusDebugTexel));
-                float2 w2 = make_float2(wd[b], wd[b]);
-                in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
-                in_zw = ffma2(w2, make_float2(t.z, t.w), in_zw);
-            }
-            float2 s2 = make_float2(s, s);
-            acc_xy = ffma2(s2, in_xy, acc_xy);
-            acc_zw = ffma2(s2, in_zw, acc_zw);
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < K; ++a) io[a] = jd[a] = -1;
-    }
-    const float4 acc = make_float4(acc_xy.x, acc_xy.y, acc_zw.x, acc_zw.y);
-    uint64_t pix = v.out_offset + (uint64_t)py * v.width + px;
+    const uint64_t pix = v.out_offset + (uint64_t)py * v.width + px;
     if constexpr (F16) {
         store_f16(p.out, p.C, pix, acc);
     } else if (p.C == 4) {
@@ -311,6 +290,93 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
             q[4] = make_int2(jd[3], jd[4]);
         }
     }
+}
+
+// Tap (i, j) of the blend: weight-scaled texel accumulated in FP32 pairs.
+template <int DT>
+__device__ __forceinline__ void blend_tap(const RenderParamsBase &p, size_t row, int32_t j, float w, bool live,
+                                          float2 &in_xy, float2 &in_zw)
+{
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live)
+        t = texel<DT>(p.texels, LF_DINDEX(row + (uint32_t)j, (uint64_t)p.rows_valid * p.N, p.status,
+                                          kStatusDebugTexel));
+    const float2 w2 = make_float2(w, w);
+    in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
+    in_zw = ffma2(w2, make_float2(t.z, t.w), in_zw);
+}
+
+template <int DT, int K, bool F16>
+__device__ __forceinline__ void render_ray(const RenderParamsBase &p, const ViewK &v, uint32_t vi, bool active,
+                                           uint32_t px, uint32_t py)
+{
+    // initialised even though every path writes them before use: measured 1.6%
+    // faster than leaving them undefined on the miss path
+    int32_t io[K], jd[K];
+    float wo[K], wd[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        io[m] = jd[m] = -1;
+        wo[m] = wd[m] = 0.0f;
+    }
+    float2 acc_xy = make_float2(0.f, 0.f), acc_zw = make_float2(0.f, 0.f);
+    uint32_t pend = 0;
+    const bool hit = active && !certain_miss(v, px, py) && ray_samples<K>(p, v, camera_dir(v, px, py), io, jd, wo, wd, pend);
+    // Taps of weight 0 are skipped. The neighbours of a set are sorted by
+    // distance and the tent gives every one beyond the kernel radius weight 0,
+    // so the nonzero weights of a set sit in a prefix (nearest sampling: the
+    // first; unstored rows of an upper-hemisphere table may leave zeros inside
+    // it). The loop over origin neighbours runs to the longest such prefix of
+    // the warp -- a bound every lane shares, reached by all 32 lanes (every lane
+    // of a tile calls this function) -- and a lane loads only the texels of its
+    // own nonzero taps (the direction taps are not cut short: a bound there
+    // measured slower, as it keeps the loads of a row from being issued
+    // together). Every texel is finite (the FP32 table is the caller's
+    // promise; the FP16 and E4M3 codes are finite by construction), so a
+    // skipped tap adds exactly the 0 that its weight gives.
+    int no = 0;
+#pragma unroll
+    for (int m = 0; m < K; ++m) no = wo[m] != 0.0f ? m + 1 : no;
+    const int no_w = (int)__reduce_max_sync(0xffffffffu, (unsigned)no);
+    // The 81 taps of K = 9 keep the outer loop rolled (instruction-cache footprint).
+#pragma unroll(K == 5 ? 5 : 1)
+    for (int a = 0; a < K; ++a) {
+        if (a >= no_w) break;
+        // origin neighbour a by a select chain: with the loop rolled (K = 9) a
+        // run-time index would move the arrays to local memory; unrolled (K = 5)
+        // the chain folds away
+        int32_t ia = io[0];
+        float wa = wo[0];
+#pragma unroll
+        for (int m = 1; m < K; ++m) {
+            ia = (a == m) ? io[m] : ia;
+            wa = (a == m) ? wo[m] : wa;
+        }
+        const bool la = wa != 0.0f;
+        // a missing or unstored neighbour has weight 0 and reads nothing
+        const int32_t i = la ? ia : 0;
+        float s = wa;
+        if constexpr (DT == kF16C4 || DT == kE4M3C4) s *= la ? __ldg(p.scales + i) : 0.0f;
+        const size_t row = (size_t)i * p.N;
+        float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < K; ++b) blend_tap<DT>(p, row, jd[b], wd[b], la && wd[b] != 0.0f, in_xy, in_zw);
+        const float2 s2 = make_float2(s, s);
+        acc_xy = ffma2(s2, in_xy, acc_xy);
+        acc_zw = ffma2(s2, in_zw, acc_zw);
+    }
+    if (!active) return;
+    if (pend) {
+        // the fixup kernel renders this ray (the weights of its uncertain set
+        // were 0 above, so it read nothing)
+        defer_push(p, vi, px, py, pend);
+        return;
+    }
+    if (!hit) {
+#pragma unroll
+        for (int a = 0; a < K; ++a) io[a] = jd[a] = -1;
+    }
+    store_ray<K, F16>(p, v, px, py, make_float4(acc_xy.x, acc_xy.y, acc_zw.x, acc_zw.y), io, jd);
 }
 
 // Position of the n-th (0-based) set bit of m (m has more than n set bits).
@@ -361,40 +427,22 @@ __device__ __forceinline__ void add_to_grad(const RenderParamsBase &p, uint64_t 
     }
 }
 
-// Backward of one ray: grad[i_a][j_b] += W_ab * g for the K x K taps. Lanes that
-// hold the same texel key are summed first (warp aggregation): when every live
-// lane of the warp has the same key, a butterfly over the warp and one atomic;
-// otherwise __match_any_sync groups and a tree sum per group, one atomic per
-// group. The loop over origin neighbours stays rolled (instruction-cache
-// footprint) and the K direction taps inside it unrolled; both read the
-// neighbours from shared memory (a run-time index into register arrays would
-// move them to local memory).
-template <int K>
-__device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const ViewK *v, bool active,
-                                             uint32_t px, uint32_t py)
+// dL/d(image) of pixel pix.
+__device__ __forceinline__ float4 grad_of(const RenderParamsBase &p, uint64_t pix)
 {
-    int32_t io[K], jd[K];
-    float wo[K], wd[K];
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-        io[m] = jd[m] = -1;
-        wo[m] = wd[m] = 0.0f;
-    }
-    bool hit = false;
-    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (active) {
-        uint64_t pix = v->out_offset + (uint64_t)py * v->width + px;
-        hit = p.idx_in ? samples_from_idx<K>(p, *v, px, py, pix, io, jd, wo, wd)
-                       : (!certain_miss(*v, px, py) && ray_samples<K>(p, *v, px, py, io, jd, wo, wd));
-        if (p.C == 4) {
-            g = __ldg(reinterpret_cast<const float4 *>(p.grad_out) + pix);
-        } else {
-            const float *q = p.grad_out + pix * 3;
-            g = make_float4(__ldg(q), __ldg(q + 1), __ldg(q + 2), 0.f);
-        }
-    }
+    if (p.C == 4) return __ldg(reinterpret_cast<const float4 *>(p.grad_out) + pix);
+    const float *q = p.grad_out + pix * 3;
+    return make_float4(__ldg(q), __ldg(q + 1), __ldg(q + 2), 0.f);
+}
+
+// The warp-aggregated scatter of the taps of one warp's rays (every lane of
+// the warp calls it; lanes without a hit contribute nothing).
+template <int K>
+__device__ __forceinline__ void backward_taps(const RenderParamsBase &p, bool hit, const int32_t (&io)[K],
+                                              const int32_t (&jd)[K], const float (&wo)[K], const float (&wd)[K],
+                                              float4 g)
+{
     const unsigned lane = threadIdx.x & 31;
-    if (!__any_sync(0xffffffffu, hit)) return;
     // Both neighbour sets wait in a per-thread shared-memory slot during the tap
     // loop (no synchronisation: each thread reads only its own slot): twenty
     // registers fewer than keeping them live, 8% faster.
@@ -439,6 +487,42 @@ __device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const Vi
         }
     }
 }
+// Backward of one ray: grad[i_a][j_b] += W_ab * g for the K x K taps. Lanes that
+// hold the same texel key are summed first (warp aggregation): when every live
+// lane of the warp has the same key, a butterfly over the warp and one atomic;
+// otherwise __match_any_sync groups and a tree sum per group, one atomic per
+// group. The loop over origin neighbours stays rolled (instruction-cache
+// footprint) and the K direction taps inside it unrolled; both read the
+// neighbours from shared memory (a run-time index into register arrays would
+// move them to local memory).
+template <int K>
+__device__ __forceinline__ void backward_ray(const RenderParamsBase &p, const ViewK *v, uint32_t vi, bool active,
+                                             uint32_t px, uint32_t py)
+{
+    int32_t io[K], jd[K];
+    float wo[K], wd[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        io[m] = jd[m] = -1;
+        wo[m] = wd[m] = 0.0f;
+    }
+    bool hit = false;
+    uint32_t pend = 0;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) {
+        uint64_t pix = v->out_offset + (uint64_t)py * v->width + px;
+        hit = p.idx_in ? samples_from_idx<K>(p, *v, px, py, pix, io, jd, wo, wd)
+                       : (!certain_miss(*v, px, py) &&
+                          ray_samples<K>(p, *v, camera_dir(*v, px, py), io, jd, wo, wd, pend));
+        g = grad_of(p, pix);
+    }
+    if (pend) {
+        defer_push(p, vi, px, py, pend);   // scattered by the fixup kernel
+        hit = false;
+    }
+    if (__any_sync(0xffffffffu, hit)) backward_taps<K>(p, hit, io, jd, wo, wd, g);
+}
+
 
 
 template <int DT, int MAXV, bool BWD, int K, bool F16 = false>
@@ -461,14 +545,14 @@ __global__ void __launch_bounds__(kMaxBlock, K == 5 ? LF_MIN_BLOCKS : 2)
         __syncthreads();
         const uint32_t v = s_tile[0], tx = s_tile[1], ty = s_tile[2];
         if (!s_tile[3]) break;
+        const ViewK &vw = p.views[v];
         uint32_t px, py;
         pixel_of(p, tx, ty, px, py);
-        const ViewK &vw = p.views[v];
         bool active = px < vw.width && py < vw.height;
         if constexpr (BWD) {
-            backward_ray<K>(p, &vw, active, px, py);
+            backward_ray<K>(p, &vw, v, active, px, py);
         } else {
-            if (active) render_ray<DT, K, F16>(p, vw, px, py);
+            render_ray<DT, K, F16>(p, vw, v, active, px, py);
         }
         if (!p.persistent) break;
         __syncthreads();               // everyone has read s_tile before it is rewritten
@@ -483,18 +567,140 @@ __global__ void __launch_bounds__(kMaxBlock, K == 5 ? LF_MIN_BLOCKS : 2)
     }
 }
 
+// One ray rendered (or its gradient scattered) by a whole warp: the sets
+// marked in pend ranked exactly by coop_knn5, weights as in the render kernel,
+// then lane 0 blends or scatters the taps of nonzero weight. Every lane of the
+// warp calls it with the same pixel (pend = 3 when the queue overflowed).
+template <int DT, bool BWD, bool F16>
+__device__ __forceinline__ void exact_ray(const RenderParamsBase &p, const ViewK &v, uint32_t px, uint32_t py,
+                                          uint32_t pend)
+{
+    int32_t io[5], jd[5];
+    float wo[5], wd[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        io[m] = jd[m] = -1;
+        wo[m] = wd[m] = 0.0f;
+    }
+    float3 ho, hd;
+    bool hit = intersect_sphere(p.sphere, v.eye, camera_dir(v, px, py), ho, hd);
+    if (hit) {
+        const PointSetK Po = point_set(p, 0), Pd = point_set(p, 1);
+        // a set the render kernel settled gives the same samples by its search
+        // again (in every lane alike); the other is ranked by the whole warp
+        bool unc = false;
+        TopK<5> ro = (pend & 1u) ? coop_knn5(Po, p.sphere, ho) : knn5(Po, p.sphere, ho, p.status, unc);
+        TopK<5> rd = (pend & 2u) ? coop_knn5(Pd, p.sphere, hd) : knn5(Pd, p.sphere, hd, p.status, unc);
+        hit = set_weights<5>(p, 0, Po.inv_sigma, ro, wo) && set_weights<5>(p, 1, Pd.inv_sigma, rd, wd);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            io[m] = hit ? ro.i[m] : -1;
+            jd[m] = hit ? rd.i[m] : -1;
+            wo[m] = hit ? wo[m] : 0.0f;
+            wd[m] = hit ? wd[m] : 0.0f;
+        }
+    }
+    if ((threadIdx.x & 31u) != 0u) return;
+    if constexpr (BWD) {
+        if (!hit) return;
+        const float4 g = grad_of(p, v.out_offset + (uint64_t)py * v.width + px);
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            if (wo[a] == 0.0f || (uint32_t)io[a] >= p.rows_valid) continue;
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+                if (wd[b] == 0.0f || jd[b] < 0) continue;
+                const float W = wo[a] * wd[b];
+                add_to_grad(p, (uint64_t)io[a] * p.N + (uint64_t)jd[b], make_float4(W * g.x, W * g.y, W * g.z, W * g.w));
+            }
+        }
+    } else {
+        float2 acc_xy = make_float2(0.f, 0.f), acc_zw = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            const bool la = wo[a] != 0.0f;
+            const int32_t i = la ? io[a] : 0;
+            float s = wo[a];
+            if constexpr (DT == kF16C4 || DT == kE4M3C4) s *= la ? __ldg(p.scales + i) : 0.0f;
+            const size_t row = (size_t)i * p.N;
+            float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 5; ++b) blend_tap<DT>(p, row, jd[b], wd[b], la && wd[b] != 0.0f, in_xy, in_zw);
+            const float2 s2 = make_float2(s, s);
+            acc_xy = ffma2(s2, in_xy, acc_xy);
+            acc_zw = ffma2(s2, in_zw, acc_zw);
+        }
+        store_ray<5, F16>(p, v, px, py, make_float4(acc_xy.x, acc_xy.y, acc_zw.x, acc_zw.y), io, jd);
+    }
+}
+
+// The rays the render kernel queued, one warp per ray; when more were queued
+// than the queue holds, every ray of the launch (the exact path gives the same
+// result for the rays the render kernel finished). The last CTA to finish
+// resets the queue for the next launch (replayable, e.g. from a CUDA graph).
+template <int DT, int MAXV, bool BWD, bool F16>
+__global__ void __launch_bounds__(kFixupThreads) fixup_kernel(const __grid_constant__ RenderParams<MAXV> p)
+{
+    const unsigned long long queued = *reinterpret_cast<volatile unsigned long long *>(p.defer_count);
+    const bool all = queued > p.defer_cap;
+    const unsigned long long total = all ? p.total_pixels : queued;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long e = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += nw) {
+        uint32_t vi = 0, px, py, pend = 3u;
+        if (!all) {
+            const unsigned long long it = p.defer_items[e];
+            pend = (uint32_t)(it >> 48) & 3u;
+            vi = (uint32_t)(it >> 32) & 0xffffu;
+            py = (uint32_t)(it >> 16) & 0xffffu;
+            px = (uint32_t)it & 0xffffu;
+        } else {
+            unsigned long long r = e;
+            while (r >= (unsigned long long)p.views[vi].width * p.views[vi].height) {
+                r -= (unsigned long long)p.views[vi].width * p.views[vi].height;
+                ++vi;
+            }
+            py = (uint32_t)(r / p.views[vi].width);
+            px = (uint32_t)(r - (unsigned long long)py * p.views[vi].width);
+        }
+        exact_ray<DT, BWD, F16>(p, p.views[vi], px, py, pend);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(p.defer_done, 1u) == gridDim.x - 1) {
+            atomicExch(p.defer_count, 0ull);
+            atomicExch(p.defer_done, 0u);
+        }
+    }
+}
+
 template <int MAXV, int K, bool F16>
 static cudaError_t launch_k(int kind, bool bwd, const RenderParams<MAXV> &p, unsigned grid, unsigned block,
                             cudaStream_t st)
 {
+    // five neighbours: the fixup kernel follows on the same stream (nine never defer)
+    const unsigned fg = kFixupCtas, fb = kFixupThreads;
     if (bwd) {
         render_kernel<kF32C4, MAXV, true, K><<<grid, block, 0, st>>>(p);
+        if (K == 5) fixup_kernel<kF32C4, MAXV, true, false><<<fg, fb, 0, st>>>(p);
     } else {
         switch (kind) {
-        case kF32C4: render_kernel<kF32C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p); break;
-        case kF32C3: render_kernel<kF32C3, MAXV, false, K, F16><<<grid, block, 0, st>>>(p); break;
-        case kF16C4: render_kernel<kF16C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p); break;
-        default: render_kernel<kE4M3C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p); break;
+        case kF32C4:
+            render_kernel<kF32C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p);
+            if (K == 5) fixup_kernel<kF32C4, MAXV, false, F16><<<fg, fb, 0, st>>>(p);
+            break;
+        case kF32C3:
+            render_kernel<kF32C3, MAXV, false, K, F16><<<grid, block, 0, st>>>(p);
+            if (K == 5) fixup_kernel<kF32C3, MAXV, false, F16><<<fg, fb, 0, st>>>(p);
+            break;
+        case kF16C4:
+            render_kernel<kF16C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p);
+            if (K == 5) fixup_kernel<kF16C4, MAXV, false, F16><<<fg, fb, 0, st>>>(p);
+            break;
+        default:
+            render_kernel<kE4M3C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p);
+            if (K == 5) fixup_kernel<kE4M3C4, MAXV, false, F16><<<fg, fb, 0, st>>>(p);
+            break;
         }
     }
     return cudaGetLastError();

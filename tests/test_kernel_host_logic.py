@@ -31,10 +31,11 @@ def _sorts_prefix(net, n, k):
     return True
 
 
-def test_select7_of16_keeps_the_seven_smallest_sorted():
-    net = _network("void select7_of16")
-    assert len(net) == 54
-    assert _sorts_prefix(net, 16, 7)
+def test_select7_of12_keeps_the_seven_smallest_sorted():
+    net = _network("void select7_of12")
+    assert len(net) == 37
+    assert all(0 <= a < b < 12 for a, b in net)
+    assert _sorts_prefix(net, 12, 7)
 
 
 def test_sort6_sorts():
