@@ -58,16 +58,39 @@ def test_lattice_offsets_follow_binet():
         assert F[k] * F[k] - F[k - 1] * F[k + 1] == (-1) ** (k + 1)
 
 
-def test_azimuth_polynomial_accuracy():
-    """The kernel's atan polynomial, evaluated in float32 as the kernel does,
-    stays within 1e-6 rad of atan2 (the lattice window tolerates 2e-3 cells, i.e. about
-    1.9e-6 rad for the largest Fibonacci step of n = 2^24 points)."""
+def _kernel_atan_coefficients():
     import numpy as np
     src = open(DEV).read()
     body = src[src.index("kAtanC[8] = {") + len("kAtanC[8] = {"):]
     body = body[:body.index("}")]
-    c = [np.float32(float(v.strip().rstrip("f"))) for v in body.split(",")]
+    return np.array([float(v.strip().rstrip("f")) for v in body.split(",")], dtype=np.float32)
+
+
+def test_azimuth_coefficients_come_from_the_fit_script():
+    """The kernel's atan coefficients are those fit_atan.py writes (minimax by
+    Lawson's algorithm, rounded to float32)."""
+    import importlib.util
+    import numpy as np
+    spec = importlib.util.spec_from_file_location("fit_atan", os.path.join(B.CSRC, "fit_atan.py"))
+    fit = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(fit)
+    c = _kernel_atan_coefficients()
     assert len(c) == 8
+    assert np.array_equal(c, fit.coefficients_f32())
+    # the fit in exact arithmetic is minimax-small, and float32 Horner stays near it
+    a = np.linspace(0.0, 1.0, 200001)
+    assert np.abs(a * np.polyval(fit.fit()[::-1], a * a) - np.arctan(a)).max() < 5e-8
+    assert np.abs(fit.eval_f32(c, a).astype(np.float64) - np.arctan(a)).max() < 2e-7
+
+
+def test_azimuth_polynomial_accuracy():
+    """The kernel's azimuth, evaluated in float32 as the kernel does (quotient,
+    polynomial, the pi/2 and pi reflections, each rounded), stays within 5e-7
+    rad of atan2 on random points of all four quadrants (the lattice window
+    tolerates 2e-3 cells, i.e. about 1.9e-6 rad for the largest Fibonacci step
+    of n = 2^24 points)."""
+    import numpy as np
+    c = _kernel_atan_coefficients()
     rng = np.random.default_rng(0)
     ang = rng.uniform(-np.pi, np.pi, 200000)
     rad = rng.uniform(1e-3, 1.0, 200000)
@@ -78,11 +101,11 @@ def test_azimuth_polynomial_accuracy():
     a2 = (a * a).astype(np.float32)
     p = np.full_like(a, c[7])
     for k in range(6, -1, -1):
-        p = (p * a2 + c[k]).astype(np.float32)
+        p = (p.astype(np.float64) * a2 + np.float64(c[k])).astype(np.float32)
     r = (a * p).astype(np.float32)
     r = np.where(ay > ax, np.float32(1.57079632679) - r, r)
     r = np.where(x < 0, np.float32(3.14159265359) - r, r)
     r = np.where(y < 0, -r, r)
     ref = np.arctan2(y.astype(np.float64), x.astype(np.float64))
     d = np.abs(np.angle(np.exp(1j * (r.astype(np.float64) - ref))))
-    assert d.max() < 1e-6
+    assert d.max() < 5e-7
