@@ -100,6 +100,7 @@ def lib():
                 "lf_struct_size": (C.c_size_t, [C.c_int]),
                 "lf_render_noalloc": (st, [C.POINTER(lf_table_desc), vp, vp, C.POINTER(lf_view), u32,
                                            C.POINTER(lf_launch), vp, vp, vp]),
+                "lf_noalloc_sync_status": (st, [vp]),
                 "lf_precompute_table": (st, [C.POINTER(lf_precompute_desc), C.POINTER(lf_blob), vp, vp]),
                 "lf_render_volume": (st, [C.POINTER(lf_precompute_desc), C.POINTER(lf_blob),
                                           C.POINTER(lf_view), u32, vp, vp]),
@@ -222,6 +223,12 @@ def lf_render_noalloc(desc: lf_table_desc, radiance_ptr: int, scales_ptr: Option
                                    views, n_views, C.byref(launch) if launch is not None else None,
                                    C.c_void_p(out_ptr), C.c_void_p(idx_ptr or None),
                                    C.c_void_p(stream or None)))
+
+
+def lf_noalloc_sync_status(stream: int = 0):
+    """Synchronise the stream and raise LfError(LF_ERR_DEVICE_CHECK) if a kernel of
+    the last lf_render_noalloc call on this device recorded a failed device check."""
+    _check(lib().lf_noalloc_sync_status(C.c_void_p(stream or None)))
 
 
 def lf_precompute_table(desc: lf_precompute_desc, blobs, out_ptr: int, stream: int = 0):
