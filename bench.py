@@ -72,12 +72,15 @@ def csrc_digest() -> str:
     return h.hexdigest()
 
 
+_WORKLOAD = {"name": "large"}
+
+
 def _recorded():
-    """The per-launch counters of the render kernel on this workload from the ncu
-    launch list summarised in profiles/render_traffic.txt; {} when the kernel
-    sources have changed since that capture."""
+    """The per-launch counters of the render kernel on the large workload from the
+    ncu launch list summarised in profiles/render_traffic.txt; {} when the kernel
+    sources have changed since that capture, or for another workload."""
     p = os.path.join(ROOT, "profiles", "render_traffic.txt")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or _WORKLOAD["name"] != "large":
         return {}
     rec = {}
     with open(p) as f:
@@ -218,6 +221,7 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev_index = torch.cuda.current_device()
     cfg = lf_inputs.config_large() if args.workload == "large" else lf_inputs.config_precision()
+    _WORKLOAD["name"] = args.workload
     lob = cfg.lobes()
     M, N = cfg.M, cfg.N
     t0 = time.time()
