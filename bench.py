@@ -705,7 +705,9 @@ def run_post_filter(args):
             "frame": "1920x1080", "filter_ms_per_frame": filt_ms, "render_ms_per_frame": render_ms,
             "filter_gpixels_s": px / (filt_ms * 1e-3) / 1e9,
             "filter_tflops": 2 * px * (4 * 16 * 9 + 16 * 16 * 9 + 16 * 3 * 9) / (filt_ms * 1e-3) / 1e12,
-            "kernel": "lfk::post_filter_kernel (FP32, CUDA cores)"}
+            "kernel": "lfk::post_filter_kernel (all three layers tcgen05.mma kind::f16, M = 128 positions x "
+                      "N = 48 (16 channels x 3 output rows) x K = 16, FP16 operands in shared memory, FP32 "
+                      "accumulators in tensor memory; a 124-column strip per CTA in bands of 6 rows, 2 CTAs per SM)"}
 
 
 def ssim_mean(ref, img, mask, data_range):

@@ -291,8 +291,12 @@ lf_status lf_render_volume(const lf_precompute_desc *desc, const lf_blob *blobs_
  * hit = 1 if the pixel's ray meets the sphere (radius, center) by the FP32 test
  * of lf_render, else 0; the result is added to the input RGB of hit pixels,
  * other pixels are set to 0, and channel 3 (channels = 4) is copied.
+ * Arithmetic: the layers run on the tensor cores with FP16 operands (the input
+ * colour clamped to +-65504, the hidden activations and the weights each
+ * rounded once to FP16) and FP32 accumulation; the residual adds the FP32
+ * input colour.
  * weights_host: LF_POST_WEIGHTS FP32 values (host, read during the call; they
- * travel in the kernel's parameters), in this order and each in
+ * travel in the kernel's parameters as FP16), in this order and each in
  * [out][in][row][column] layout: W1 [16][4][3][3], b1 [16], W2 [16][16][3][3],
  * b2 [16], W3 [3][16][3][3], b3 [3]. in_dev / out_dev: [pixels][channels] FP32
  * (device; views laid out as for lf_render, channels 3 or 4; 4-byte aligned);

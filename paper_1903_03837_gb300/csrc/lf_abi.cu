@@ -701,7 +701,10 @@ lf_status lf_post_filter(double radius, const double center[3], uint32_t channel
     cudaStream_t st = (cudaStream_t)stream;
     for (uint32_t v0 = 0; v0 < n_views; v0 += lfk::kPostMaxViews) {
         const uint32_t nv = n_views - v0 < (uint32_t)lfk::kPostMaxViews ? n_views - v0 : (uint32_t)lfk::kPostMaxViews;
-        for (uint32_t v = 0; v < nv; ++v) p.views[v] = lfk::camera_of(views[v0 + v]);
+        for (uint32_t v = 0; v < nv; ++v) {
+            p.views[v] = lfk::camera_of(views[v0 + v]);
+            lfk::fill_view_miss_consts(p.views[v], radius, center);   // the certain hit/miss tests of the mask
+        }
         p.n_views = nv;
         cudaError_t e = lfk::launch_post_filter(p, st);
         if (e != cudaSuccess) return cuda_fail(e, "post-filter");

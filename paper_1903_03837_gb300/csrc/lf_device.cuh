@@ -149,6 +149,27 @@ __device__ __forceinline__ bool certain_miss(const ViewK &v, uint32_t x, uint32_
     return no_disc || away;
 }
 
+// The hit mask of a pixel's ray by the approximate ray of certain_miss, where
+// it is certain: 0 if the ray certainly misses S, 1 if it certainly hits S in
+// front of the eye (discriminant above 0 and direction towards the centre,
+// both by the relative margin 1e-4, so the exact step would report the same),
+// -1 if only the exact ray/sphere step can tell.
+__device__ __forceinline__ int approx_mask(const ViewK &v, uint32_t x, uint32_t y)
+{
+    if (!v.outside) return -1;
+    float nx = __fmaf_rn(__uint2float_rn(x) + 0.5f, v.inv2w, -1.0f) * v.tan_x;
+    float ny = __fmaf_rn(-(__uint2float_rn(y) + 0.5f), v.inv2h, 1.0f) * v.tan_y;
+    float vx = __fmaf_rn(ny, v.up[0], __fmaf_rn(nx, v.right[0], v.fwd[0]));
+    float vy = __fmaf_rn(ny, v.up[1], __fmaf_rn(nx, v.right[1], v.fwd[1]));
+    float vz = __fmaf_rn(ny, v.up[2], __fmaf_rn(nx, v.right[2], v.fwd[2]));
+    float b = __fmaf_rn(v.f0[0], vx, __fmaf_rn(v.f0[1], vy, v.f0[2] * vz));
+    float vv = __fmaf_rn(vx, vx, __fmaf_rn(vy, vy, vz * vz));
+    float b2 = b * b, vc = vv * v.c0, m = 1e-4f * sqrtf(vv * v.ff0);
+    if ((b2 - vc) < -1e-4f * (b2 + vc) || b > m) return 0;
+    if ((b2 - vc) > 1e-4f * (b2 + vc) && b < -m) return 1;
+    return -1;
+}
+
 // ---------------------------------------------------------------------------
 // Double-float arithmetic (value = hi + lo, about 48 significant bits).
 // ---------------------------------------------------------------------------

@@ -112,8 +112,8 @@ cudaError_t launch_volume_direct(const PrecomputeParams &p, const ViewK &v, cons
 
 // lf_post.cu: the learned post-filter of the light-field image. Weights in
 // framework (OIHW) order, FP32: W1 [16][4][3][3], b1 [16], W2 [16][16][3][3],
-// b2 [16], W3 [3][16][3][3], b3 [3]; they travel in the kernel's parameter
-// block, so every multiply-add reads its weight as a constant-bank operand.
+// b2 [16], W3 [3][16][3][3], b3 [3]; launch_post_filter lays them out as the
+// FP16 B operands of the kernel's MMAs, which travel in its parameter block.
 constexpr int kPostHidden = 16;
 constexpr int kPostW1 = 0;
 constexpr int kPostB1 = kPostW1 + kPostHidden * 4 * 9;
@@ -129,11 +129,10 @@ struct PostParams {
     float *out;                         // [P][C] filtered image (must not overlap `in`)
     uint32_t C;                         // 3 or 4 (channel 3 is copied)
     uint32_t n_views;
-    uint32_t tile_prefix[kPostMaxViews + 1];   // filled by launch_post_filter
-    ViewK views[kPostMaxViews];         // cameras; tiles_x, tiles_y filled by launch_post_filter
+    ViewK views[kPostMaxViews];         // cameras
     float w[kPostWeights];
 };
-// Tiles the views (at most kPostMaxViews) and launches the filter.
+// Splits the views (at most kPostMaxViews) into strips and chunks and launches the filter.
 cudaError_t launch_post_filter(const PostParams &p, cudaStream_t st);
 
 // Fills the conservative-miss constants of a view for sphere (R, O) (lf_abi.cu).
