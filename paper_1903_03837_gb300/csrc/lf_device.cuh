@@ -145,7 +145,8 @@ __device__ __forceinline__ bool certain_miss(const ViewK &v, uint32_t x, uint32_
     float vv = __fmaf_rn(vx, vx, __fmaf_rn(vy, vy, vz * vz));
     float b2 = b * b, vc = vv * v.c0;
     bool no_disc = (b2 - vc) < -1e-4f * (b2 + vc);
-    bool away = b > 1e-4f * sqrtf(vv * v.ff0);
+    // b > 1e-4 |v| |f0|, compared in squares (no square root)
+    bool away = b > 0.0f && b2 > 1e-8f * (vv * v.ff0);
     return no_disc || away;
 }
 
@@ -975,6 +976,16 @@ __device__ __forceinline__ TopK<9> knn9(const PointSetK &P, const SphereK &S, fl
 
 // Tent weights of one set of K neighbours, normalised to sum 1 (nearest takes
 // all if none is inside the kernel radius).
+// 1/x by the hardware approximation (within 1 ulp; x here is a sum of tent
+// weights, in (0, 9]): the weights carry a tolerance, not the bits of an IEEE
+// division.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int K>
 __device__ __forceinline__ void tent_weights(const float (&d2)[K], int cnt, float inv_sigma, float (&w)[K])
 {
@@ -987,7 +998,7 @@ __device__ __forceinline__ void tent_weights(const float (&d2)[K], int cnt, floa
         S += v;
     }
     if (S > 0.0f) {
-        float r = __frcp_rn(S);
+        const float r = rcp_approx(S);
 #pragma unroll
         for (int m = 0; m < K; ++m) w[m] *= r;
     } else {
@@ -1016,7 +1027,7 @@ __device__ __forceinline__ bool tent_weights_kept(const float (&d2)[K], const in
     }
     if (first < 0) return false;
     if (S > 0.0f) {
-        float r = __frcp_rn(S);
+        const float r = rcp_approx(S);
 #pragma unroll
         for (int m = 0; m < K; ++m) w[m] *= r;
     } else {

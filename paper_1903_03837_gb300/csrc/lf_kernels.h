@@ -18,7 +18,7 @@ constexpr uint32_t kStripTiles = 4;
 // count of queued rays; the queued rays follow at byte kWordsBytes.
 constexpr uint32_t kWordsBytes = 256;
 constexpr uint32_t kDeferCap = 1u << 18;         // queued rays a table holds per launch
-constexpr unsigned kFixupCtas = 304, kFixupThreads = 256;
+constexpr unsigned kFixupCtas = 304, kFixupThreads = 256;   // the fixup grid when the occupancy query fails
 constexpr uint32_t kFixupWarps = kFixupThreads / 32;
 
 struct RenderParamsBase {

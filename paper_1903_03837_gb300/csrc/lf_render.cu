@@ -674,32 +674,53 @@ __global__ void __launch_bounds__(kFixupThreads) fixup_kernel(const __grid_const
     }
 }
 
+// Grid of a fixup kernel: as many CTAs as its registers let the SMs hold at
+// once (a few queued rays per warp at most), found once per device and thread.
+template <int DT, int MAXV, bool BWD, bool F16>
+static unsigned fixup_grid()
+{
+    static thread_local int dev_cached = -1;
+    static thread_local unsigned grid = kFixupCtas;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return kFixupCtas;
+    if (dev != dev_cached) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fixup_kernel<DT, MAXV, BWD, F16>,
+                                                          (int)kFixupThreads, 0) == cudaSuccess &&
+            sms > 0 && per_sm > 0)
+            grid = (unsigned)(sms * per_sm);
+        dev_cached = dev;
+    }
+    return grid;
+}
+
 template <int MAXV, int K, bool F16>
 static cudaError_t launch_k(int kind, bool bwd, const RenderParams<MAXV> &p, unsigned grid, unsigned block,
                             cudaStream_t st)
 {
     // five neighbours: the fixup kernel follows on the same stream (nine never defer)
-    const unsigned fg = kFixupCtas, fb = kFixupThreads;
+    const unsigned fb = kFixupThreads;
     if (bwd) {
         render_kernel<kF32C4, MAXV, true, K><<<grid, block, 0, st>>>(p);
-        if (K == 5) fixup_kernel<kF32C4, MAXV, true, false><<<fg, fb, 0, st>>>(p);
+        if (K == 5) fixup_kernel<kF32C4, MAXV, true, false><<<fixup_grid<kF32C4, MAXV, true, false>(), fb, 0, st>>>(p);
     } else {
         switch (kind) {
         case kF32C4:
             render_kernel<kF32C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p);
-            if (K == 5) fixup_kernel<kF32C4, MAXV, false, F16><<<fg, fb, 0, st>>>(p);
+            if (K == 5) fixup_kernel<kF32C4, MAXV, false, F16><<<fixup_grid<kF32C4, MAXV, false, F16>(), fb, 0, st>>>(p);
             break;
         case kF32C3:
             render_kernel<kF32C3, MAXV, false, K, F16><<<grid, block, 0, st>>>(p);
-            if (K == 5) fixup_kernel<kF32C3, MAXV, false, F16><<<fg, fb, 0, st>>>(p);
+            if (K == 5) fixup_kernel<kF32C3, MAXV, false, F16><<<fixup_grid<kF32C3, MAXV, false, F16>(), fb, 0, st>>>(p);
             break;
         case kF16C4:
             render_kernel<kF16C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p);
-            if (K == 5) fixup_kernel<kF16C4, MAXV, false, F16><<<fg, fb, 0, st>>>(p);
+            if (K == 5) fixup_kernel<kF16C4, MAXV, false, F16><<<fixup_grid<kF16C4, MAXV, false, F16>(), fb, 0, st>>>(p);
             break;
         default:
             render_kernel<kE4M3C4, MAXV, false, K, F16><<<grid, block, 0, st>>>(p);
-            if (K == 5) fixup_kernel<kE4M3C4, MAXV, false, F16><<<fg, fb, 0, st>>>(p);
+            if (K == 5) fixup_kernel<kE4M3C4, MAXV, false, F16><<<fixup_grid<kE4M3C4, MAXV, false, F16>(), fb, 0, st>>>(p);
             break;
         }
     }
