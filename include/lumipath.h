@@ -73,11 +73,13 @@ typedef struct lf_table_desc {
 } lf_table_desc;
 
 /* A pinhole camera. Pixel (x, y) of a W x H image looks along
- *   v = forward + ((2(x+0.5))/W - 1) * tan_half_x * right
- *               + (1 - (2(y+0.5))/H) * tan_half_y * up,
- * normalised, from `eye`; every operation is one FP32 IEEE operation in
- * exactly this order (no fused multiply-add). Row 0 is the top of the image.
- * The pixel's output goes to out[out_offset + y*W + x]. */
+ *   v = forward + ((x+0.5) * s_w - 1) * tan_half_x * right
+ *               + (1 - (y+0.5) * s_h) * tan_half_y * up,
+ *   d = v * (1 / sqrt(v.v)),
+ * from `eye`, where s_w = 2/W and s_h = 2/H are rounded to FP32 once; every
+ * other operation is one FP32 IEEE operation in exactly this order (no fused
+ * multiply-add). Row 0 is the top of the image. The pixel's output goes to
+ * out[out_offset + y*W + x]. */
 typedef struct lf_view {
     float eye[3];
     float right[3];

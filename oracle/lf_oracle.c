@@ -74,22 +74,26 @@ void lfo_sf_points(uint32_t n, double *out /* [n][3] */)
 /* ------------------------------------------------------------------------- */
 /* Camera ray (pinhole), FP32, fixed order. A view is 14 floats:              */
 /* eye[3], right[3], up[3], forward[3], tan_half_x, tan_half_y.               */
-/* Pixel centres at +0.5; row 0 is the top of the image (+up).                */
+/* Pixel centres at +0.5; row 0 is the top of the image (+up). The paper      */
+/* only asks for one rasterisation ray per pixel (Section 2); this library    */
+/* fixes its arithmetic: the pixel centre times 2/W (2/H) rounded to FP32     */
+/* once, the direction times the rounded reciprocal of its length.            */
 /* ------------------------------------------------------------------------- */
 void lfo_camera_ray(const float *vw, uint32_t W, uint32_t H, uint32_t x, uint32_t y,
                     float dir[3])
 {
     const float *right = vw + 3, *up = vw + 6, *fwd = vw + 9;
+    const float s2w = (float)(2.0 / (double)W), s2h = (float)(2.0 / (double)H);
     float px = (float)x + 0.5f, py = (float)y + 0.5f;
-    float sx = (px + px) / (float)W;
-    float sy = (py + py) / (float)H;
+    float sx = px * s2w;
+    float sy = py * s2h;
     float nx = (sx - 1.0f) * vw[12];
     float ny = (1.0f - sy) * vw[13];
     float v[3];
     for (int k = 0; k < 3; ++k) v[k] = (fwd[k] + nx * right[k]) + ny * up[k];
     float l2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
-    float l = sqrtf(l2);
-    for (int k = 0; k < 3; ++k) dir[k] = v[k] / l;
+    float il = 1.0f / sqrtf(l2);
+    for (int k = 0; k < 3; ++k) dir[k] = v[k] * il;
 }
 
 /* Ray / sphere S (Section 2): front hit h_o and back hit h_d. Returns 0 for a */

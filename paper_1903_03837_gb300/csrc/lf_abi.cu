@@ -173,6 +173,8 @@ ViewK camera_of(const lf_view &w)
     k.width = w.width;
     k.height = w.height;
     k.out_offset = w.out_offset;
+    k.inv2w = (float)(2.0 / w.width);        // the camera ray's pixel scale, and the miss test's
+    k.inv2h = (float)(2.0 / w.height);
     return k;
 }
 
@@ -327,8 +329,6 @@ void fill_view_miss_consts(ViewK &k, double R, const double O[3])
     for (int i = 0; i < 3; ++i) k.f0[i] = (float)f[i];
     k.ff0 = (float)ff;
     k.c0 = (float)(ff - R * R);
-    k.inv2w = (float)(2.0 / k.width);
-    k.inv2h = (float)(2.0 / k.height);
     k.outside = (ff - R * R) > 1e-3 * ff ? 1u : 0u;
 }
 

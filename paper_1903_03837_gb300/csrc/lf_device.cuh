@@ -76,11 +76,15 @@ __device__ __forceinline__ float azimuth_turns(float y, float x)
 // ---------------------------------------------------------------------------
 // The camera ray's direction before normalisation is the column term
 // fwd + nx*right of pixel column x plus the row term ny*up of pixel row y (in
-// this operation order), so a tile can compute its columns and rows once.
+// this operation order), so a tile can compute its columns and rows once. The
+// pixel centre x + 1/2 is scaled by 2/W rounded to FP32 once per view
+// (ViewK::inv2w; 2/H likewise), and the direction is normalised by one
+// correctly rounded reciprocal of its length: every step an IEEE FP32
+// operation, so a CPU reproduces the ray bit for bit.
 __device__ __forceinline__ float3 camera_col(const ViewK &v, uint32_t x)
 {
     float px = __fadd_rn(__uint2float_rn(x), 0.5f);
-    float sx = __fdiv_rn(__fadd_rn(px, px), __uint2float_rn(v.width));
+    float sx = __fmul_rn(px, v.inv2w);
     float nx = __fmul_rn(__fsub_rn(sx, 1.0f), v.tan_x);
     return make_float3(__fadd_rn(v.fwd[0], __fmul_rn(nx, v.right[0])), __fadd_rn(v.fwd[1], __fmul_rn(nx, v.right[1])),
                        __fadd_rn(v.fwd[2], __fmul_rn(nx, v.right[2])));
@@ -88,7 +92,7 @@ __device__ __forceinline__ float3 camera_col(const ViewK &v, uint32_t x)
 __device__ __forceinline__ float3 camera_row(const ViewK &v, uint32_t y)
 {
     float py = __fadd_rn(__uint2float_rn(y), 0.5f);
-    float sy = __fdiv_rn(__fadd_rn(py, py), __uint2float_rn(v.height));
+    float sy = __fmul_rn(py, v.inv2h);
     float ny = __fmul_rn(__fsub_rn(1.0f, sy), v.tan_y);
     return make_float3(__fmul_rn(ny, v.up[0]), __fmul_rn(ny, v.up[1]), __fmul_rn(ny, v.up[2]));
 }
@@ -97,8 +101,8 @@ __device__ __forceinline__ float3 camera_dir_cr(float3 c, float3 r)
 {
     float vx = __fadd_rn(c.x, r.x), vy = __fadd_rn(c.y, r.y), vz = __fadd_rn(c.z, r.z);
     float l2 = __fadd_rn(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)), __fmul_rn(vz, vz));
-    float l = __fsqrt_rn(l2);
-    return make_float3(__fdiv_rn(vx, l), __fdiv_rn(vy, l), __fdiv_rn(vz, l));
+    float il = __frcp_rn(__fsqrt_rn(l2));
+    return make_float3(__fmul_rn(vx, il), __fmul_rn(vy, il), __fmul_rn(vz, il));
 }
 __device__ __forceinline__ float3 camera_dir(const ViewK &v, uint32_t x, uint32_t y)
 {

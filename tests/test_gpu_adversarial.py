@@ -200,7 +200,10 @@ def test_chord_views_hit_their_targets():
             b = -b
         hit, _, _, _, qo, qd = oracle.trace_pixel(1.0, (0.0, 0.0, 0.0), v, 0, 0)
         assert hit
-        assert np.linalg.norm(qo - a) < 2e-6 and np.linalg.norm(qd - b) < 2e-6
+        # the FP32 view basis and ray aim within about 1e-7 of the chord; the
+        # FP32 discriminant (|e|^2 up to 12, one rounding about 1e-6) moves the
+        # hits by up to ~1e-6 / (half the chord), 2.4e-6 on these chords
+        assert np.linalg.norm(qo - a) < 5e-6 and np.linalg.norm(qd - b) < 5e-6
 
 
 def test_ties_survive_the_fp32_ray():
