@@ -978,8 +978,6 @@ __device__ __forceinline__ TopK<9> knn9(const PointSetK &P, const SphereK &S, fl
     return r;
 }
 
-// Tent weights of one set of K neighbours, normalised to sum 1 (nearest takes
-// all if none is inside the kernel radius).
 // 1/x by the hardware approximation (within 1 ulp; x here is a sum of tent
 // weights, in (0, 9]): the weights carry a tolerance, not the bits of an IEEE
 // division.
@@ -990,6 +988,8 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// Tent weights of one set of K neighbours, normalised to sum 1 (nearest takes
+// all if none is inside the kernel radius).
 template <int K>
 __device__ __forceinline__ void tent_weights(const float (&d2)[K], int cnt, float inv_sigma, float (&w)[K])
 {
