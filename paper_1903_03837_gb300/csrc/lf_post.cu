@@ -23,7 +23,10 @@
 // swizzle: 16 contiguous bytes hold eight FP16 channels of one position), so a
 // tap's shift is just another start address; the input's second K chunk is the
 // next position (leading byte offset 16), so one MMA takes the taps dx and
-// dx + 1 (dx = 0, 2; the weights of dx = 3 are zero).
+// dx + 1 (dx = 0, 2; the weights of dx = 3 are zero). The third layer has 3
+// output channels: its one MMA per operand row holds all three horizontal taps
+// in N (16 columns per output row: 3 dx x 3 channels, 9 used) on the unshifted
+// row, and its epilogue adds the taps dx = 1, 2 from the next positions' lanes.
 //
 // A CTA of 256 threads walks down one strip of 124 output columns of one view
 // over a chunk of its rows. Every step adds kBand rows to each layer: it loads
@@ -58,7 +61,7 @@ constexpr int kHRing = kBand + 2;                   // the kBand + 2 rows of the
 constexpr int kInBytes = (kInRing * kRow + 1) * 16; // FP16 [row][position][8], one zero position after the last
 constexpr int kHChunk = kHRing * kRow * 16;         // one 8-channel chunk of a hidden layer's ring
 constexpr int kWGroup = 1536;                       // one MMA's 48 x 16 FP16 weights: [K chunk][n 48][8 k]
-constexpr int kWBytes = 8 * kWGroup;                // layer 1: 2 tap pairs; layers 2, 3: 3 taps each
+constexpr int kWBytes = 6 * kWGroup;                // layer 1: 2 tap pairs; layer 2: 3 taps; layer 3: 1
 constexpr size_t kOffH1 = (kInBytes + 127) / 128 * 128, kOffH2 = kOffH1 + 2 * kHChunk, kOffW = kOffH2 + 2 * kHChunk;
 constexpr size_t kPostSmem = kOffW + kWBytes;
 constexpr int kBlocks = kBand + 4;                  // accumulator blocks: output rows -2 .. kBand + 1 of a layer
@@ -70,6 +73,7 @@ constexpr int kBandPix = kBand * kRow;              // input positions loaded pe
 constexpr int kLoadIters = (kBandPix + kPostThreads - 1) / kPostThreads;
 static_assert(kBlocks * 16 <= (int)kTmemCols && kHRing >= 7 && kBand + 1 < kInRing, "ring and tensor-memory sizes");
 static_assert(2 * (kPostSmem + 1024) <= 228 * 1024, "two CTAs per SM");
+static_assert(kBand == 2 * kRowsPerWarp, "every warp takes kRowsPerWarp rows of a step");
 
 // The kernel's parameters: the launch's views split into strips and chunks,
 // the biases and the FP16 B operands of the MMAs (post_weight_image).
@@ -221,7 +225,8 @@ __device__ __forceinline__ void epilogue16(uint32_t taddr, int t0, const float *
 // Issues one layer's MMAs: operand row rho (0 .. kBand + 1, the layer below's
 // row t0 + rho, ring slot s0 + rho of a ring of n rows) at tap group gr into
 // accumulator blocks rho .. rho + 2 (N = 48). GROUPS = 3: gr = dx; GROUPS = 2
-// (the input): gr = the tap pair dx = 2 gr, 2 gr + 1. The rows go 0, 3, 6, 1,
+// (the input): gr = the tap pair dx = 2 gr, 2 gr + 1; GROUPS = 1 (the third
+// layer): the row unshifted, its three taps dx in the B operand's columns. The rows go 0, 3, 6, 1,
 // 4, 7, 2, 5, so consecutive MMAs write disjoint blocks. The descriptors'
 // start addresses advance in 16-byte units.
 template <int GROUPS>
@@ -287,6 +292,7 @@ __global__ void __launch_bounds__(kPostThreads, 2) post_filter_kernel(const __gr
     __shared__ uint32_t s_tile[3];
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ float s_edge[2][kRowsPerWarp][4][9];   // third layer: lanes 0, 1 of each 32 positions
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t mbar = smem_addr(&s_mbar);
     if (tid == 0) {
@@ -397,35 +403,71 @@ __global__ void __launch_bounds__(kPostThreads, 2) post_filter_kernel(const __gr
         epilogue16(taddr, t2, p.bias + kPostHidden, x0 - 1, ya - 1, W, H, done, s_h2);
         ok = handover_sync(done);
 
-        // layer 3: output rows t3 .. (3 of 16 columns used) from second-layer rows t3 .. t3 + kBand + 1
+        // layer 3: output rows t3 .. from second-layer rows t3 .. t3 + kBand + 1, one MMA per
+        // operand row: its 16 columns per output row are (dx, channel), 9 used, unshifted
         if (tid == 0 && ok) {
-            issue_layer<3>(taddr, a_h2, b_w3, ring(t3, kHRing), kHRing);
+            issue_layer<1>(taddr, a_h2, b_w3, ring(t3, kHRing), kHRing);
             mma_commit(mbar);
         }
         done = ok && wait_phase(mbar, phase);
         phase ^= ok ? 1u : 0u;
         ok = done;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // bias, added to the input colour of hit pixels; NaN if the MMAs never
-        // completed; the blocks back to zero for the next step's first layer
-        uint32_t a[kRowsPerWarp][4];
-#pragma unroll
-        for (int i = 0; i < kRowsPerWarp; ++i)
-            if (g + 2 * i < kBand) tmem_ld4(taddr + ((uint32_t)(32 * q) << 16) + 16 * (g + 2 * i + 2), a[i]);
-        tmem_wait<4, kRowsPerWarp>(a);
-#pragma unroll
-        for (int i = 0; i < kRowsPerWarp; ++i)
-            if (g + 2 * i < kBand) tmem_zero16(taddr + ((uint32_t)(32 * q) << 16) + 16 * (g + 2 * i + 2));
+        // The third layer's accumulator row of position p holds, in column
+        // 3 dx + c, channel c of tap dx applied at position p; the output at p
+        // sums column 3 dx + c of position p + dx (dx = 0, 1, 2). Within a warp
+        // the shifted columns come by shuffles; lanes 30 and 31 take them from
+        // lanes 0 and 1 of the next 32 positions through shared memory (a
+        // barrier of the row group's four warps). Then the bias, added to the
+        // input colour of hit pixels; NaN if the MMAs never completed; the
+        // blocks back to zero for the next step's first layer.
 #pragma unroll
         for (int i = 0; i < kRowsPerWarp; ++i) {
-            const int t = t3 + g + 2 * i;
-            if (g + 2 * i >= kBand || !col_ok || t < 0 || t >= rows) continue;
+            const int r = g + 2 * i, t = t3 + r;
+            uint32_t hv[1][16];
+            const uint32_t blk = taddr + ((uint32_t)(32 * q) << 16) + 16 * (r + 2);
+            tmem_ld16(blk, hv[0]);
+            tmem_wait<16, 1>(hv);
+            tmem_zero16(blk);
+            float f[9];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) f[c] = __uint_as_float(hv[0][c]);
+            float *edge = s_edge[g][i][q];
+            if (lane == 0) {
+#pragma unroll
+                for (int c = 3; c < 9; ++c) edge[c] = f[c];
+            } else if (lane == 1) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) edge[c] = f[6 + c];
+            }
+            if (g == 0)
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            else
+                asm volatile("bar.sync 2, 128;" ::: "memory");
+            float o1[3], o2[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o1[c] = __shfl_down_sync(0xffffffffu, f[3 + c], 1);
+                o2[c] = __shfl_down_sync(0xffffffffu, f[6 + c], 2);
+            }
+            if (q < 3 && lane >= 30) {
+                const float *next = s_edge[g][i][q + 1];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    o1[c] = lane == 31 ? next[3 + c] : o1[c];
+                    o2[c] = lane == 31 ? next[c] : next[6 + c];
+                }
+            }
+            if (!col_ok || t < 0 || t >= rows) continue;
             const __half2 bm = *reinterpret_cast<const __half2 *>(s_in + (ring(t + 3, kInRing) * kRow + pos + 3) * 16 + 4);
             const bool hit = __high2float(bm) != 0.0f;
+            float a3[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a3[c] = __fadd_rn(__fadd_rn(f[c], o1[c]), o2[c]) + p.bias[2 * kPostHidden + c];
             float4 o;
-            o.x = hit ? res[i].x + (__uint_as_float(a[i][0]) + p.bias[2 * kPostHidden]) : 0.0f;
-            o.y = hit ? res[i].y + (__uint_as_float(a[i][1]) + p.bias[2 * kPostHidden + 1]) : 0.0f;
-            o.z = hit ? res[i].z + (__uint_as_float(a[i][2]) + p.bias[2 * kPostHidden + 2]) : 0.0f;
+            o.x = hit ? res[i].x + a3[0] : 0.0f;
+            o.y = hit ? res[i].y + a3[1] : 0.0f;
+            o.z = hit ? res[i].z + a3[2] : 0.0f;
             o.w = res[i].w;
             if (!done) o.x = o.y = o.z = __int_as_float(0x7fc00000);
             float *out = p.out + (v.out_offset + (uint64_t)(ya + t) * W + xout) * p.C;
@@ -452,13 +494,13 @@ __global__ void __launch_bounds__(kPostThreads, 2) post_filter_kernel(const __gr
 // The B operands of the kernel's MMAs, FP16, [group][K chunk c][n][k] with
 // n = 16 s + o (output channel o of the output row fed through kernel row
 // dy = 2 - s): layer 1 (groups 0, 1: the tap pair dx = 2 gr + c, input
-// channel k < 4, zero for dx = 3 and k >= 4), then layers 2 and 3 (groups
-// 2..4 and 5..7: tap dx = group, input channel 8 c + k; zero for o >= 3 in
-// layer 3).
+// channel k < 4, zero for dx = 3 and k >= 4), layer 2 (groups 2..4: tap
+// dx = group, input channel 8 c + k) and layer 3 (group 5: column o = 3 dx +
+// output channel, all three taps dx, zero for o >= 9).
 static void post_weight_image(const float *w, uint4 *img)
 {
     uint16_t *h = reinterpret_cast<uint16_t *>(img);
-    for (int gr = 0; gr < 8; ++gr)
+    for (int gr = 0; gr < 6; ++gr)
         for (int c = 0; c < 2; ++c)
             for (int n = 0; n < 48; ++n)
                 for (int k = 0; k < 8; ++k) {
@@ -469,8 +511,9 @@ static void post_weight_image(const float *w, uint4 *img)
                         if (k < 4 && dx < 3) x = w[kPostW1 + ((o * 4 + k) * 3 + dy) * 3 + dx];
                     } else if (gr < 5) {
                         x = w[kPostW2 + ((o * kPostHidden + 8 * c + k) * 3 + dy) * 3 + (gr - 2)];
-                    } else if (o < 3) {
-                        x = w[kPostW3 + ((o * kPostHidden + 8 * c + k) * 3 + dy) * 3 + (gr - 5)];
+                    } else if (o < 9) {
+                        const int dx = o / 3, ch = o - 3 * dx;
+                        x = w[kPostW3 + ((ch * kPostHidden + 8 * c + k) * 3 + dy) * 3 + dx];
                     }
                     const __half hx = __float2half_rn(x);
                     memcpy(&h[(gr * kWGroup + c * 768 + n * 16 + k * 2) / 2], &hx, 2);
