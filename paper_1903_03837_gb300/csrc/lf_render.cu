@@ -297,10 +297,11 @@ template <int DT>
 __device__ __forceinline__ void blend_tap(const RenderParamsBase &p, size_t row, int32_t j, float w, bool live,
                                           float2 &in_xy, float2 &in_zw)
 {
-    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (live)
-        t = texel<DT>(p.texels, LF_DINDEX(row + (uint32_t)j, (uint64_t)p.rows_valid * p.N, p.status,
-                                          kStatusDebugTexel));
+    // a dead tap reads the row's first texel (finite) with weight 0: a branch
+    // around the load costs more than the load, which hits L1
+    const float4 t = texel<DT>(p.texels, LF_DINDEX(row + (uint32_t)(live ? j : 0), (uint64_t)p.rows_valid * p.N,
+                                                   p.status, kStatusDebugTexel));
+    w = live ? w : 0.0f;
     const float2 w2 = make_float2(w, w);
     in_xy = ffma2(w2, make_float2(t.x, t.y), in_xy);
     in_zw = ffma2(w2, make_float2(t.z, t.w), in_zw);
@@ -328,12 +329,12 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
     // first; unstored rows of an upper-hemisphere table may leave zeros inside
     // it). The loop over origin neighbours runs to the longest such prefix of
     // the warp -- a bound every lane shares, reached by all 32 lanes (every lane
-    // of a tile calls this function) -- and a lane loads only the texels of its
-    // own nonzero taps (the direction taps are not cut short: a bound there
-    // measured slower, as it keeps the loads of a row from being issued
-    // together). Every texel is finite (the FP32 table is the caller's
-    // promise; the FP16 and E4M3 codes are finite by construction), so a
-    // skipped tap adds exactly the 0 that its weight gives.
+    // of a tile calls this function); within it a lane's taps of weight 0 read
+    // the row's first texel, without a branch (the direction taps are not cut
+    // short: a bound there measured slower, as it keeps the loads of a row from
+    // being issued together). Every texel is finite (the FP32 table is the
+    // caller's promise; the FP16 and E4M3 codes are finite by construction),
+    // so a dead tap adds exactly the 0 that its weight gives.
     int no = 0;
 #pragma unroll
     for (int m = 0; m < K; ++m) no = wo[m] != 0.0f ? m + 1 : no;
@@ -462,7 +463,9 @@ __device__ __forceinline__ void backward_taps(const RenderParamsBase &p, bool hi
         for (int b = 0; b < K; ++b) {
             const int32_t jb = s_bw[(2 * K + b) * kMaxBlock + threadIdx.x];
             const float wb = __int_as_float(s_bw[(3 * K + b) * kMaxBlock + threadIdx.x]);
-            bool live = hit && (uint32_t)ia < p.rows_valid && jb >= 0;
+            // a tap of weight 0 (beyond the kernel radius in either set) would add
+            // exactly 0: it takes no atomic
+            bool live = hit && (uint32_t)ia < p.rows_valid && jb >= 0 && wa != 0.0f && wb != 0.0f;
             uint64_t key = live ? (uint64_t)ia * p.N + (uint64_t)jb : 0ull;
             float W = live ? wa * wb : 0.f;
             float4 val = make_float4(W * g.x, W * g.y, W * g.z, W * g.w);
