@@ -295,11 +295,12 @@ __device__ __forceinline__ void store_ray(const RenderParamsBase &p, const ViewK
 // Tap (i, j) of the blend: weight-scaled texel accumulated in FP32 pairs.
 template <int DT>
 __device__ __forceinline__ void blend_tap(const RenderParamsBase &p, size_t row, int32_t j, float w, bool live,
-                                          float2 &in_xy, float2 &in_zw)
+                                          int32_t j0, float2 &in_xy, float2 &in_zw)
 {
-    // a dead tap reads the row's first texel (finite) with weight 0: a branch
-    // around the load costs more than the load, which hits L1
-    const float4 t = texel<DT>(p.texels, LF_DINDEX(row + (uint32_t)(live ? j : 0), (uint64_t)p.rows_valid * p.N,
+    // a dead tap reads column j0 of its row (finite) with weight 0: a branch
+    // around the load costs more than the load; j0 is the lane's nearest
+    // direction, so in a live row that texel is loaded anyway (an L1 hit)
+    const float4 t = texel<DT>(p.texels, LF_DINDEX(row + (uint32_t)(live ? j : j0), (uint64_t)p.rows_valid * p.N,
                                                    p.status, kStatusDebugTexel));
     w = live ? w : 0.0f;
     const float2 w2 = make_float2(w, w);
@@ -361,7 +362,8 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
         const size_t row = (size_t)i * p.N;
         float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int b = 0; b < K; ++b) blend_tap<DT>(p, row, jd[b], wd[b], la && wd[b] != 0.0f, in_xy, in_zw);
+        for (int b = 0; b < K; ++b)
+            blend_tap<DT>(p, row, jd[b], wd[b], la && wd[b] != 0.0f, max(jd[0], 0), in_xy, in_zw);
         const float2 s2 = make_float2(s, s);
         acc_xy = ffma2(s2, in_xy, acc_xy);
         acc_zw = ffma2(s2, in_zw, acc_zw);
@@ -628,7 +630,8 @@ __device__ __forceinline__ void exact_ray(const RenderParamsBase &p, const ViewK
             const size_t row = (size_t)i * p.N;
             float2 in_xy = make_float2(0.f, 0.f), in_zw = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int b = 0; b < 5; ++b) blend_tap<DT>(p, row, jd[b], wd[b], la && wd[b] != 0.0f, in_xy, in_zw);
+            for (int b = 0; b < 5; ++b)
+                blend_tap<DT>(p, row, jd[b], wd[b], la && wd[b] != 0.0f, max(jd[0], 0), in_xy, in_zw);
             const float2 s2 = make_float2(s, s);
             acc_xy = ffma2(s2, in_xy, acc_xy);
             acc_zw = ffma2(s2, in_zw, acc_zw);
