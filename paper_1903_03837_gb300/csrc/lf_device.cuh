@@ -947,21 +947,20 @@ __device__ __forceinline__ TopK<9> knn9(const PointSetK &P, const SphereK &S, fl
     const float e = tier1_err(fminf(__uint_as_float(s10[9] | mask1), 4.5f));
     bool order1 = true;
 #pragma unroll
-    for (int m = 0; m < 9; ++m) {
-        if (s10[m + 1] != kNone) {
-            const float lb = __uint_as_float(s10[m + 1] & ~mask1) - e;
-            const float ub = __uint_as_float(s10[m] | mask1) + e;
-            order1 &= (lb - ub) > 0x1p-40f;
-        }
+    for (int m = 0; m < 9; ++m) {   // no branches here or below (as in knn5)
+        const float lb = __uint_as_float(s10[m + 1] & ~mask1) - e;
+        const float ub = __uint_as_float(s10[m] | mask1) + e;
+        order1 &= (s10[m + 1] == kNone) | ((lb - ub) > 0x1p-40f);
     }
     TopK<9> r;
     r.cnt = 0;
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
-        bool ok = s10[m] != kNone;
-        int32_t i = ok ? source_index9(src, (int)(s10[m] & mask1)) : 0;
+        const bool ok = s10[m] != kNone;
+        const int32_t i = ok ? source_index9(src, (int)(s10[m] & mask1)) : 0;
+        const float d2 = dist2_df(P, i, qh, ql);
         r.i[m] = ok ? i : -1;
-        r.d2[m] = ok ? dist2_df(P, i, qh, ql) : 0.0f;
+        r.d2[m] = ok ? d2 : 0.0f;
         r.cnt += ok ? 1 : 0;
     }
     if (!order1) {
