@@ -359,6 +359,31 @@ __device__ __forceinline__ void sort6(uint32_t k[6])
     LF_CS(0, 3) LF_CS(2, 5) LF_CS(1, 3) LF_CS(2, 4) LF_CS(2, 3)
 }
 
+// The 10 smallest of 25 keys, sorted into k[0..9]: Batcher's odd-even merge
+// sort of 32 inputs with inputs 25..31 fixed at +inf, pruned to the
+// comparators that reach outputs 0..9 (119 comparators, against 250
+// compare-exchanges for inserting the 25 keys into a sorted list of 10).
+__device__ __forceinline__ void select10_of25(uint32_t k[25])
+{
+    LF_CS(0, 1) LF_CS(2, 3) LF_CS(0, 2) LF_CS(1, 3) LF_CS(1, 2) LF_CS(4, 5) LF_CS(6, 7)
+    LF_CS(4, 6) LF_CS(5, 7) LF_CS(5, 6) LF_CS(0, 4) LF_CS(2, 6) LF_CS(2, 4) LF_CS(1, 5)
+    LF_CS(3, 7) LF_CS(3, 5) LF_CS(1, 2) LF_CS(3, 4) LF_CS(5, 6) LF_CS(8, 9) LF_CS(10, 11)
+    LF_CS(8, 10) LF_CS(9, 11) LF_CS(9, 10) LF_CS(12, 13) LF_CS(14, 15) LF_CS(12, 14) LF_CS(13, 15)
+    LF_CS(13, 14) LF_CS(8, 12) LF_CS(10, 14) LF_CS(10, 12) LF_CS(9, 13) LF_CS(11, 15) LF_CS(11, 13)
+    LF_CS(9, 10) LF_CS(11, 12) LF_CS(13, 14) LF_CS(0, 8) LF_CS(4, 12) LF_CS(4, 8) LF_CS(2, 10)
+    LF_CS(6, 14) LF_CS(6, 10) LF_CS(2, 4) LF_CS(6, 8) LF_CS(10, 12) LF_CS(1, 9) LF_CS(5, 13)
+    LF_CS(5, 9) LF_CS(3, 11) LF_CS(7, 15) LF_CS(7, 11) LF_CS(3, 5) LF_CS(7, 9) LF_CS(11, 13)
+    LF_CS(1, 2) LF_CS(3, 4) LF_CS(5, 6) LF_CS(7, 8) LF_CS(9, 10) LF_CS(11, 12) LF_CS(16, 17)
+    LF_CS(18, 19) LF_CS(16, 18) LF_CS(17, 19) LF_CS(17, 18) LF_CS(20, 21) LF_CS(22, 23) LF_CS(20, 22)
+    LF_CS(21, 23) LF_CS(21, 22) LF_CS(16, 20) LF_CS(18, 22) LF_CS(18, 20) LF_CS(17, 21) LF_CS(19, 23)
+    LF_CS(19, 21) LF_CS(17, 18) LF_CS(19, 20) LF_CS(21, 22) LF_CS(16, 24) LF_CS(20, 24) LF_CS(18, 20)
+    LF_CS(22, 24) LF_CS(19, 21) LF_CS(17, 18) LF_CS(19, 20) LF_CS(21, 22) LF_CS(23, 24) LF_CS(0, 16)
+    LF_CS(8, 24) LF_CS(8, 16) LF_CS(4, 20) LF_CS(12, 20) LF_CS(4, 8) LF_CS(12, 16) LF_CS(2, 18)
+    LF_CS(10, 18) LF_CS(6, 22) LF_CS(6, 10) LF_CS(2, 4) LF_CS(6, 8) LF_CS(10, 12) LF_CS(1, 17)
+    LF_CS(9, 17) LF_CS(5, 21) LF_CS(5, 9) LF_CS(3, 19) LF_CS(11, 19) LF_CS(7, 23) LF_CS(7, 11)
+    LF_CS(3, 5) LF_CS(7, 9) LF_CS(1, 2) LF_CS(3, 4) LF_CS(5, 6) LF_CS(7, 8) LF_CS(9, 10)
+}
+
 __device__ __forceinline__ void insert7(uint32_t s[7], uint32_t key)
 {
 #pragma unroll
@@ -931,13 +956,17 @@ __device__ __forceinline__ TopK<9> knn9(const PointSetK &P, const SphereK &S, fl
 #pragma unroll
     for (int m = 0; m < 10; ++m) s10[m] = kNone;
     if (src.scan_cnt == 0) {
-#pragma unroll 5
+        uint32_t k[kWindow9];
+#pragma unroll
         for (int s = 0; s < kWindow9; ++s) {
-            int32_t i = window_index25(src, s);
-            bool ok = (uint32_t)i < (uint32_t)n;
-            float dd = dist2_hi(P, ok ? i : 0, qh);
-            insert_sorted(s10, ok ? ((__float_as_uint(dd) & ~mask1) | (uint32_t)s) : kNone);
+            const int32_t i = window_index25(src, s);
+            const bool ok = (uint32_t)i < (uint32_t)n;
+            const float dd = dist2_hi(P, ok ? i : 0, qh);
+            k[s] = ok ? ((__float_as_uint(dd) & ~mask1) | (uint32_t)s) : kNone;
         }
+        select10_of25(k);
+#pragma unroll
+        for (int m = 0; m < 10; ++m) s10[m] = k[m];
     } else {
         for (int s = 0; s < src.scan_cnt; ++s)
             insert_sorted(s10, (__float_as_uint(dist2_hi(P, src.b0 + s, qh)) & ~mask1) | (uint32_t)s);

@@ -38,6 +38,36 @@ def test_select7_of12_keeps_the_seven_smallest_sorted():
     assert _sorts_prefix(net, 12, 7)
 
 
+def _sorts_prefix_packed(net, n, k):
+    """The 0-1 principle over all 2^n binary inputs, 64 inputs per machine
+    word: line i holds bit i of every input index; a comparator is AND (min)
+    and OR (max); output m must be 1 exactly for the inputs with at most m
+    zeros."""
+    import numpy as np
+    idx = np.arange(1 << n, dtype=np.uint32)
+    lines = [np.packbits(((idx >> i) & 1).astype(np.uint8), bitorder="little").view(np.uint64) for i in range(n)]
+    for a, b in net:
+        lines[a], lines[b] = lines[a] & lines[b], lines[a] | lines[b]
+    zeros = n - np.bitwise_count(idx).astype(np.int64)
+    for m in range(k):
+        want = np.packbits((zeros <= m).astype(np.uint8), bitorder="little").view(np.uint64)
+        if not np.array_equal(lines[m], want):
+            return False
+    return True
+
+
+def test_select10_of25_keeps_the_ten_smallest_sorted():
+    net = _network("void select10_of25")
+    assert len(net) == 119
+    assert all(0 <= a < b < 25 for a, b in net)
+    assert _sorts_prefix_packed(net, 25, 10)
+
+
+def test_packed_check_rejects_a_broken_network():
+    net = _network("void select10_of25")
+    assert not _sorts_prefix_packed(net[:-1], 25, 10)
+
+
 def test_sort6_sorts():
     net = _network("void sort6")
     assert len(net) == 12
