@@ -572,32 +572,22 @@ __device__ __forceinline__ Top5 knn5(const PointSetK &P, const SphereK &S, float
     for (int m = 0; m < 5; ++m)   // no branches here or below: they cost more than the work they skip
         order1 &= (s7[m + 1] == kNone) |
                   (__fsub_rn(__uint_as_float(s7[m + 1] & ~mask1), __uint_as_float(s7[m] | mask1)) > gap);
+    // Double-float distances of the tier-1 top 5: the result's weights when the
+    // certificate holds, tier 2's input otherwise (an empty slot reads point 0
+    // and discards it)
     Top5 r;
     r.cnt = 0;
-    if (order1) {
-        // Double-float distances of the 5 for their weights (an empty slot
-        // reads point 0 and discards it).
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const bool ok = s7[m] != kNone;
-            const int32_t i = ok ? source_index(src, s7[m] & mask1) : 0;
-            const float d2 = dist2_df(P, LF_DINDEX(i, P.n, status, kStatusDebugPoint), qh, ql);
-            r.i[m] = ok ? i : -1;
-            r.d2[m] = ok ? d2 : 0.0f;
-            r.cnt += ok ? 1 : 0;
-        }
-        return r;
+    for (int m = 0; m < 5; ++m) {
+        const bool ok = s7[m] != kNone;
+        const int32_t i = ok ? source_index(src, s7[m] & mask1) : 0;
+        const float d2 = dist2_df(P, LF_DINDEX(i, P.n, status, kStatusDebugPoint), qh, ql);
+        r.i[m] = ok ? i : -1;
+        r.d2[m] = ok ? d2 : 0.0f;
+        r.cnt += ok ? 1 : 0;
     }
+    if (order1) return r;
     {
-        // Double-float distances of the tier-1 top 5.
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const bool ok = s7[m] != kNone;
-            const int32_t i = ok ? source_index(src, s7[m] & mask1) : 0;
-            r.i[m] = ok ? i : -1;
-            r.d2[m] = ok ? dist2_df(P, LF_DINDEX(i, P.n, status, kStatusDebugPoint), qh, ql) : 0.0f;
-            r.cnt += ok ? 1 : 0;
-        }
         // Tier 2: the top 6 in double-float, sorted, when the tier-1 bounds put
         // the true 5 nearest among them (the 5th's upper bound below the 7th's
         // lower bound, with the error bound taken at the 7th key). Accepted when
