@@ -117,6 +117,11 @@ __device__ __forceinline__ float4 march(const PrecomputeParams &p, float ox, flo
 
     float T = 1.0f;
     if (dt > 0.0f) {
+        // dt folded into the densities: g' = g dt = 2^(la + log2 dt - y^2), so the
+        // step's optical depth is sum g' and its weight T (1 - e^-x) / x
+        const float l2dt = __log2f(dt);
+#pragma unroll
+        for (int k = 0; k < BMAX; ++k) la[k] += l2dt;
 #if LF_PRE_PACKED
         // blobs in pairs: y, y^2, the exponent, the density sum and the
         // per-blob weights in packed FP32 pairs
@@ -141,10 +146,10 @@ __device__ __forceinline__ float4 march(const PrecomputeParams &p, float ox, flo
                 g2[q] = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
                 sig2 = add2(sig2, g2[q]);
             }
-            // step of constant density: weight T (1 - e^-x) / sigma = T dt (1 - e^-x) / x
-            const float xs = (sig2.x + sig2.y) * dt;
+            // step of constant density: x = sigma dt, weight T (1 - e^-x) / x per g'
+            const float xs = sig2.x + sig2.y;
             const float E = ex2_approx(-xs * kLog2e);
-            const float w = T * one_minus_exp_over_x(xs, E) * dt;
+            const float w = T * one_minus_exp_over_x(xs, E);
             const float2 w2 = make_float2(w, w);
 #pragma unroll
             for (int q = 0; q < BP; ++q) G2[q] = fma2(w2, g2[q], G2[q]);
@@ -166,10 +171,10 @@ __device__ __forceinline__ float4 march(const PrecomputeParams &p, float ox, flo
                 g[k] = ex2_approx(fmaf(-y, y, la[k]));
                 sig += g[k];
             }
-            // step of constant density: weight T (1 - e^-x) / sigma = T dt (1 - e^-x) / x
-            const float xs = sig * dt;
+            // step of constant density: x = sigma dt, weight T (1 - e^-x) / x per g'
+            const float xs = sig;
             const float E = ex2_approx(-xs * kLog2e);
-            const float w = T * one_minus_exp_over_x(xs, E) * dt;
+            const float w = T * one_minus_exp_over_x(xs, E);
 #pragma unroll
             for (int k = 0; k < BMAX; ++k) G[k] = fmaf(w, g[k], G[k]);
             T *= E;
