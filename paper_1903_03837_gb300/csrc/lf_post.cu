@@ -37,9 +37,9 @@
 // layer keeps its last rows in a ring in shared memory, so no row is computed
 // twice except the six rows before the chunk; the rows of the first step
 // that lie before it are computed from rows never loaded and are only ever
-// read for outputs before the chunk, which are not stored. A CTA needs 96 KB
-// of shared memory and 128 tensor-memory columns, so two share an SM and each
-// runs its loads and epilogues while the other's MMAs run. The MMAs of each
+// read for outputs before the chunk, which are not stored. A CTA needs 95 KB
+// of shared memory and 256 tensor-memory columns (half an SM's), so two share
+// an SM and each runs its loads and epilogues while the other's MMAs run. The MMAs of each
 // row produce 128 positions and the valid width shrinks by 2 per layer (130
 // input positions, 128 first-layer, 126 second-layer, 124 output columns).
 #include <cuda_fp16.h>
