@@ -324,18 +324,18 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
     float2 acc_xy = make_float2(0.f, 0.f), acc_zw = make_float2(0.f, 0.f);
     uint32_t pend = 0;
     const bool hit = active && !certain_miss(v, px, py) && ray_samples<K>(p, v, camera_dir(v, px, py), io, jd, wo, wd, pend);
-    // Taps of weight 0 are skipped. The neighbours of a set are sorted by
-    // distance and the tent gives every one beyond the kernel radius weight 0,
-    // so the nonzero weights of a set sit in a prefix (nearest sampling: the
-    // first; unstored rows of an upper-hemisphere table may leave zeros inside
-    // it). The loop over origin neighbours runs to the longest such prefix of
-    // the warp -- a bound every lane shares, reached by all 32 lanes (every lane
-    // of a tile calls this function); within it a lane's taps of weight 0 read
-    // the row's first texel, without a branch (the direction taps are not cut
-    // short: a bound there measured slower, as it keeps the loads of a row from
-    // being issued together). Every texel is finite (the FP32 table is the
-    // caller's promise; the FP16 and E4M3 codes are finite by construction),
-    // so a dead tap adds exactly the 0 that its weight gives.
+    // Origin rows past every lane's last tap of weight > 0 are skipped. The
+    // neighbours of a set are sorted by distance and the tent gives every one
+    // beyond the kernel radius weight 0, so the nonzero weights of a set sit in
+    // a prefix (nearest sampling: the first; unstored rows of an upper-hemisphere
+    // table may leave zeros inside it). The loop over origin neighbours runs to
+    // the longest such prefix of the warp -- a bound every lane shares, reached
+    // by all 32 lanes (every lane of a tile calls this function); within it a
+    // lane's taps of weight 0 read, without a branch, its nearest direction
+    // column of the row (the direction taps are not cut short: a bound there
+    // measured slower). Every texel is finite (the FP32 table is the caller's
+    // promise; the FP16 and E4M3 codes are finite by construction), so a dead
+    // tap adds exactly the 0 that its weight gives.
     int no = 0;
 #pragma unroll
     for (int m = 0; m < K; ++m) no = wo[m] != 0.0f ? m + 1 : no;
@@ -355,7 +355,7 @@ __device__ __forceinline__ void render_ray(const RenderParamsBase &p, const View
             wa = (a == m) ? wo[m] : wa;
         }
         const bool la = wa != 0.0f;
-        // a missing or unstored neighbour has weight 0 and reads nothing
+        // a missing or unstored neighbour has weight 0 and reads within row 0
         const int32_t i = la ? ia : 0;
         float s = wa;
         if constexpr (DT == kF16C4 || DT == kE4M3C4) s *= la ? __ldg(p.scales + i) : 0.0f;
